@@ -1,0 +1,98 @@
+"""Pins for the oracle's SVGD update [Eq. svgd], bandwidth and Adam.
+
+* the lower-median bandwidth agrees with scipy's pairwise distances;
+* the repulsive term equals the autograd gradient of the RBF kernel in its
+  first argument (sign and the 2/h factor), the attractive term a plain
+  kernel-weighted mean;
+* with one particle the update is plain Adam on grad log p (torch.optim.Adam);
+* SVGD fits a 1-D Gaussian target: mean and variance of the particles;
+* the distinct-plan top-k on hand-made cases.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.spatial.distance import pdist
+
+from oracle import stamp_oracle as O
+
+
+def test_median_bandwidth_matches_scipy_lower_median():
+    rng = np.random.default_rng(0)
+    for n in (2, 3, 17, 64):
+        th = rng.standard_normal((n, 5))
+        vals = np.sort(pdist(th, "sqeuclidean"))
+        assert abs(O.median_bandwidth(th) - vals[(vals.size - 1) // 2] / math.log(n + 1)) < 1e-12
+
+
+def test_bandwidth_degenerate_cases():
+    assert O.median_bandwidth(np.ones((1, 4))) == 1.0
+    assert O.median_bandwidth(np.ones((5, 4))) == 1.0     # all distances zero
+
+
+def test_stein_direction_against_autograd_kernel_gradient():
+    rng = np.random.default_rng(1)
+    n, d = 9, 4
+    th = rng.standard_normal((n, d))
+    g = rng.standard_normal((n, d))
+    h = 0.7
+    phi = O.stein_direction(th, g, h)
+    T = torch.tensor(th, requires_grad=True)
+    ref = np.zeros((n, d))
+    for i in range(n):
+        for j in range(n):
+            tj = T[j].detach().clone().requires_grad_(True)
+            kji = torch.exp(-((tj - T[i].detach()) ** 2).sum() / h)
+            (gk,) = torch.autograd.grad(kji, tj)
+            ref[i] += float(kji.detach()) * g[j] + gk.numpy()
+    assert np.allclose(phi, ref / n, rtol=1e-12, atol=1e-12)
+
+
+def test_single_particle_svgd_is_adam_on_grad_log_p():
+    rng = np.random.default_rng(2)
+    th = rng.standard_normal((1, 6))
+    x = torch.tensor(th.copy(), requires_grad=True)
+    opt = torch.optim.Adam([x], lr=0.05)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for step in range(1, 30):
+        g = -(th - 0.3) * 2.0                                 # grad log p of a Gaussian
+        th, m, v, h, phi = O.svgd_step(th, g, m, v, step, 0.05)
+        assert h == 1.0 and np.allclose(phi, g, rtol=1e-13)
+        opt.zero_grad()
+        x.grad = torch.tensor(-(-(x.detach().numpy() - 0.3) * 2.0))
+        opt.step()
+        assert np.allclose(th, x.detach().numpy(), rtol=1e-12, atol=1e-13)
+
+
+def test_sgd_phase_follows_grad_log_p():
+    rng = np.random.default_rng(3)
+    th = rng.standard_normal((7, 3))
+    g = rng.standard_normal((7, 3))
+    th2, _, _, h, phi = O.svgd_step(th, g, np.zeros_like(th), np.zeros_like(th), 1, 0.01, sgd_phase=True)
+    assert np.array_equal(phi, g)
+    # first Adam step moves every coordinate by lr along sign(phi)
+    assert np.allclose(th2 - th, 0.01 * np.sign(g), rtol=1e-6)
+
+
+def test_svgd_fits_1d_gaussian():
+    """SVGD with the RBF kernel and median bandwidth recovers N(mu, s^2)."""
+    mu, s = 1.5, 0.7
+    th = np.random.default_rng(4).uniform(-3, 3, size=(512, 1))
+    for _ in range(1500):
+        g = -(th - mu) / s ** 2
+        h = O.median_bandwidth(th)
+        th = th + 0.05 * O.stein_direction(th, g, h)
+    assert abs(th.mean() - mu) < 0.02 * s
+    assert abs(th.var() - s * s) < 0.05 * s * s
+
+
+def test_topk_distinct_plans():
+    costs = np.array([0.5, 0.1, 0.1, 0.3, 0.2, 0.05])
+    codes = np.array([[0, 1], [2, 2], [2, 2], [0, 1], [3, 0], [2, 2]])
+    # order by (cost, index): 5, 1, 2, 4, 3, 0 -> plans (2,2), (3,0), (0,1)
+    assert O.topk_plans(costs, codes, 3) == [5, 4, 3]
+    assert O.topk_plans(costs, codes, 5) == [5, 4, 3, -1, -1]
+    # equal costs: the lower index wins
+    assert O.topk_plans(np.array([1.0, 1.0]), np.array([[0], [1]]), 1) == [0]
