@@ -1,0 +1,273 @@
+"""Throughput of STAMP's hot path on GB300: particle rollout+adjoint steps/s.
+
+One step = one stamp_solve call: Algorithm 1 over the workload's particles
+(every SVGD iteration = Gumbel-relaxed forward rollout, checkpointed adjoint,
+median bandwidth, Stein direction, Adam), then the hard evaluation and the
+distinct-plan top-k.  One unit = one particle advanced one substep forward and
+back, so a step is N*H*T*iterations units.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
+
+Under torchrun every rank solves its own seeded instance (no collective on the
+data path: the instances are independent); value = all ranks' units divided
+by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle rollout+adjoint steps/s"
+UNIT = "particle-substeps/s"
+# Algorithmic FLOPs per unit (one particle, one substep), counted over the
+# oracle's own operations (oracle/flops.py): forward, reverse sweep.
+FLOPS_PER_UNIT = {1: (447.2, 863.2), 2: None, 3: (6293.5, 12860.9)}
+SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes, 1 FMA = 2 FLOP
+KERNEL_IDS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("sm_max_mhz", 2070.0), d.get("hbm_gbs", 6775.6), "measured"
+    return 2070.0, 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def cpu_oracle_sample(P, init, goal, seed, n_particles, iters=1):
+    """Time the FP64 oracle on a bounded sample: n_particles of the workload,
+    `iters` iterations of rollout + reverse sweep + Stein step."""
+    import torch
+    from oracle import stamp_oracle as O
+    M, _, D = O.dims(P)
+    th = O.init_theta(seed, n_particles, D)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    t0 = time.perf_counter()
+    for it in range(iters):
+        gum = O.gumbel_noise(seed, it, n_particles, P["H"], M)
+        _, g = O.rollout_grad(th, P, init, goal, gum)
+        th, m, v, _, _ = O.svgd_step(th, g, m, v, it + 1, P["lr"])
+    dt = time.perf_counter() - t0
+    units = n_particles * P["H"] * P["T"] * iters
+    return units / dt, dt, torch.get_num_threads()
+
+
+def run_reference(args, P, world, rank):
+    """The reference arm: the oracle as it stands on the host cores."""
+    if rank != 0:
+        return
+    init, goal = __import__("paper_2310_01775_gb300.workloads", fromlist=["W"]).scene(P, args.seed)
+    n = args.ref_particles
+    for _ in range(args.warmup):
+        cpu_oracle_sample(P, init, goal, args.seed, max(2, n // 8))
+    times, vals = [], []
+    for s in range(args.steps):
+        v, dt, cores = cpu_oracle_sample(P, init, goal, args.seed + s, n)
+        times.append(dt)
+        vals.append(v)
+    units = n * P["H"] * P["T"]
+    value = units * len(times) / sum(times)
+    sample = f"{n} of {P['N']} particles, 1 iteration per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, P),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, P):
+    iters = P["svgd_iters"]
+    return {"workload": (f"{args.workload}: {P['n_blocks']} block(s), H={P['H']}, T={P['T']}, "
+                         f"N={P['N']}, D={P['H'] * (4 * P['n_blocks'] + 2)}, {iters} SVGD "
+                         f"iterations + hard evaluation + top-3 per step"),
+            "ckpt_every": P["ckpt_every"], "l2_flush": "256 MiB write between steps",
+            "units_per_step": P["N"] * P["H"] * P["T"] * iters}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="pusher1_h4")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--ref-particles", type=int, default=32)
+    ap.add_argument("--baseline-particles", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, nargs=2, default=None)
+    ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval override")
+    args = ap.parse_args()
+
+    from paper_2310_01775_gb300 import workloads as W
+    P = W.params(args.workload, **({"ckpt_every": args.ckpt} if args.ckpt else {}))
+    world, rank, local = dist_setup() if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        run_reference(args, P, world, rank)
+        return
+
+    import torch
+    from paper_2310_01775_gb300 import stamp as S
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    seed = args.seed + 1000 * rank
+    init, goal = W.scene(P, seed)
+    N, H, T, iters = P["N"], P["H"], P["T"], P["svgd_iters"]
+    prob = S.Problem(P, init, goal, N, stream.cuda_stream)
+    if args.lanes:
+        prob.set_lanes(*args.lanes)
+    D = prob.D
+    th = torch.empty(N, D, device=dev)
+    cost = torch.empty(N, device=dev)
+    topk = np.zeros(3, dtype=np.int32)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    units = N * H * T * iters
+
+    def step(s):
+        prob.solve(N, iters, 0, seed + s, P["lr"], None, th, cost, 3, topk, None)
+
+    for s in range(args.warmup):
+        step(s)
+    # timed region: per-step CUDA events on the problem's stream, L2 flushed in between
+    prob.set_profiling(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    evs = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(args.warmup + s)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    kt = prob.kernel_times()
+    prob.set_profiling(False)
+    t_max = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    ms_max = float(t_max)
+    value = units * args.steps * world / (ms_max / 1e3)
+
+    # end to end through the public call with host buffers (pinned)
+    th_h = torch.empty(N, D, pin_memory=True)
+    th0_h = torch.tensor(W.random_theta(N, D, seed), dtype=torch.float32).pin_memory()
+    cost_h = torch.empty(N, pin_memory=True)
+    e2e_t = []
+    for s in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.solve(N, iters, 0, seed + s, P["lr"], th0_h, th_h, cost_h, 3, topk, None)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": units / min(e2e_t), "unit": UNIT, "h2d_bytes_per_step": N * D * 4,
+           "d2h_bytes_per_step": N * D * 4 + N * 4 + 3 * 4}
+
+    if rank != 0:
+        prob.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (FP32 ALU bound; FLOPs from the oracle count)
+    dom = max(kt, key=lambda k: kt[k][0])
+    mhz, hbm, src = peaks()
+    peak_tflops = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    fpu = FLOPS_PER_UNIT.get(P["n_blocks"])
+    roof = None
+    if fpu and dom in ("rollout_fwd", "rollout_adj") and kt[dom][1]:
+        per_launch_ms = kt[dom][0] / kt[dom][1]
+        # the hard evaluation is also a forward launch: weight by the relaxed ones
+        flops = (fpu[0] if dom == "rollout_fwd" else fpu[1]) * N * H * T
+        ach = flops / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": ach / peak_tflops, "traffic": None,
+                "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz ({src})",
+                "ms_per_launch": per_launch_ms}
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, dt, cores = cpu_oracle_sample(P, init, goal, seed, args.baseline_particles)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.baseline_particles} of {N} particles, 1 iteration ({dt:.1f} s)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, P), "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clocks, "e2e": e2e,
+            "gpu_launches": int(sum(n for _, n in kt.values())),
+            "kernels_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}}
+    print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -84,9 +84,10 @@ def sm64(key, ctr):
         return _mix(key + (ctr + np.uint64(1)) * GAMMA)
 
 
-def uniform24(x):
-    """Top 24 bits of a 64-bit draw as a float in (0, 1): ((x>>40)+0.5)/2^24."""
-    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(40)).astype(np.float64) + 0.5) * 2.0 ** -24
+def uniform23(x):
+    """Top 23 bits of a 64-bit draw as a float in (0, 1): ((x>>41)+0.5)/2^23,
+    a value that float32 represents exactly."""
+    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(41)).astype(np.float64) + 0.5) * 2.0 ** -23
 
 
 def gumbel_noise(seed: int, it: int, n: int, H: int, M: int) -> np.ndarray:
@@ -97,7 +98,7 @@ def gumbel_noise(seed: int, it: int, n: int, H: int, M: int) -> np.ndarray:
     """
     key = sm64(sm64(np.uint64(seed), STREAM_GUMBEL), np.uint64(it))
     ctr = np.arange(n * H * M, dtype=np.uint64).reshape(n, H, M)
-    u = uniform24(sm64(key, ctr))
+    u = uniform23(sm64(key, ctr))
     return -np.log(-np.log(u))
 
 
@@ -106,7 +107,7 @@ def init_theta(seed: int, n: int, d: int) -> np.ndarray:
     of App. A.1.  Draw number i*d + j of the key chain seed -> stream 1."""
     key = sm64(np.uint64(seed), STREAM_INIT)
     ctr = np.arange(n * d, dtype=np.uint64).reshape(n, d)
-    return 2.0 * uniform24(sm64(key, ctr)) - 1.0
+    return 2.0 * uniform23(sm64(key, ctr)) - 1.0
 
 
 # ----------------------------------------------------------------------------

@@ -1,0 +1,17 @@
+// Rollout kernels for scenes of 2 block(s): one instantiation per supported lane count.
+#include "rollout.cuh"
+
+namespace stamp {
+
+cudaError_t launch_rollout_nb2(const SimConst& sc, const RolloutArgs& a, int lanes, bool adjoint,
+                                 cudaStream_t st) {
+    switch (lanes) {
+        case 2: return rollout::launch<2, 2>(sc, a, adjoint, st);
+        case 4: return rollout::launch<2, 4>(sc, a, adjoint, st);
+        case 8: return rollout::launch<2, 8>(sc, a, adjoint, st);
+        case 16: return rollout::launch<2, 16>(sc, a, adjoint, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace stamp

@@ -1,0 +1,16 @@
+// Rollout kernels for scenes of 4 block(s): one instantiation per supported lane count.
+#include "rollout.cuh"
+
+namespace stamp {
+
+cudaError_t launch_rollout_nb4(const SimConst& sc, const RolloutArgs& a, int lanes, bool adjoint,
+                                 cudaStream_t st) {
+    switch (lanes) {
+        case 8: return rollout::launch<4, 8>(sc, a, adjoint, st);
+        case 16: return rollout::launch<4, 16>(sc, a, adjoint, st);
+        case 32: return rollout::launch<4, 32>(sc, a, adjoint, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace stamp

@@ -1,0 +1,503 @@
+// C ABI of the STAMP hot path (declared in include/stamp.h): problem
+// objects, argument checks, the Algorithm 1 loop and kernel timing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "stamp.h"
+#include "stamp_internal.cuh"
+
+using stamp::SimConst;
+
+namespace {
+
+thread_local std::string g_err;
+
+stamp_status fail(stamp_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define STAMP_CUDA(call)                                                                 \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(STAMP_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+constexpr int kMaxParticles = 16384;     // d2 scratch is N^2 floats (1 GiB at the cap)
+constexpr long long kMaxStatsIters = 1 << 20;
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct stamp_problem {
+    SimConst sc;
+    int max_n = 0;
+    cudaStream_t stream = nullptr;
+    // one device arena, carved into the buffers below
+    char* arena = nullptr;
+    float *tape = nullptr, *cost = nullptr, *grad = nullptr, *theta = nullptr, *m = nullptr,
+          *v = nullptr, *phi = nullptr, *d2 = nullptr, *h = nullptr, *one = nullptr;
+    unsigned *hist = nullptr, *stats = nullptr;
+    int *flag = nullptr, *topk = nullptr;
+    unsigned long long* dropped = nullptr;
+    // last forward
+    bool have_tape = false;
+    int last_n = 0, last_iter = 0, last_hard = 0;
+    unsigned long long last_seed = 0;
+    const float* last_theta = nullptr;
+    int fwd_lanes = 0, adj_lanes = 0;
+    // kernel timing
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;          // pairs (start, stop)
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    double ms[STAMP_NKERNELS] = {};
+    long long launches[STAMP_NKERNELS] = {};
+};
+
+namespace {
+
+template <class F>
+stamp_status timed(stamp_problem* p, int kind, F&& launch) {
+    const bool rec = p->prof && p->ev_used < p->ev_kind.size();
+    if (rec) STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used], p->stream));
+    const cudaError_t e = launch();
+    if (e != cudaSuccess) return fail(STAMP_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    if (rec) {
+        STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used + 1], p->stream));
+        p->ev_kind[p->ev_used++] = kind;
+    }
+    return STAMP_OK;
+}
+
+// After a stream sync: fold the recorded event pairs into the totals.
+stamp_status collect(stamp_problem* p) {
+    for (size_t q = 0; q < p->ev_used; ++q) {
+        float t = 0.f;
+        STAMP_CUDA(cudaEventElapsedTime(&t, p->ev[2 * q], p->ev[2 * q + 1]));
+        p->ms[p->ev_kind[q]] += t;
+        p->launches[p->ev_kind[q]] += 1;
+    }
+    p->ev_used = 0;
+    return STAMP_OK;
+}
+
+stamp_status check_flag(stamp_problem* p) {
+    int f = 0;
+    STAMP_CUDA(cudaMemcpy(&f, p->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        STAMP_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
+        return fail(STAMP_ENONFINITE, "a non-finite particle or Stein direction was produced");
+    }
+    return STAMP_OK;
+}
+
+int lanes_for(const stamp_problem* p, int N, bool adj) {
+    const int want = adj ? p->adj_lanes : p->fwd_lanes;
+    return want ? want : stamp::default_lanes(p->sc.nb, N, adj);
+}
+
+stamp_status check_n(const stamp_problem* p, int N) {
+    if (N < 1 || N > p->max_n) return fail(STAMP_EINVAL, "N=%d outside [1, %d]", N, p->max_n);
+    return STAMP_OK;
+}
+
+stamp_status check_dev(const void* ptr, const char* name, bool allow_null = false) {
+    if (!ptr) return allow_null ? STAMP_OK : fail(STAMP_EINVAL, "%s is NULL", name);
+    if (!is_device_ptr(ptr)) return fail(STAMP_EINVAL, "%s is not device memory", name);
+    return STAMP_OK;
+}
+
+#define STAMP_TRY(x)                      \
+    do {                                  \
+        stamp_status s_ = (x);            \
+        if (s_ != STAMP_OK) return s_;    \
+    } while (0)
+
+stamp_status fwd(stamp_problem* p, const float* theta, int N, unsigned long long seed, int iter,
+                 int hard, float* cost, float* final_state, unsigned* stats_word) {
+    stamp::RolloutArgs a{};
+    a.theta = theta; a.N = N; a.seed = seed; a.iter = iter; a.hard = hard;
+    a.tape = p->tape; a.cost = cost; a.final_state = final_state; a.stats_min = stats_word;
+    const int lanes = lanes_for(p, N, false);
+    STAMP_TRY(timed(p, STAMP_K_ROLLOUT_FWD,
+                    [&] { return stamp::launch_rollout_fwd(p->sc, a, lanes, p->stream); }));
+    p->have_tape = true;
+    p->last_n = N; p->last_seed = seed; p->last_iter = iter; p->last_hard = hard;
+    p->last_theta = theta;
+    return STAMP_OK;
+}
+
+stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
+    stamp::RolloutArgs a{};
+    a.theta = theta; a.N = N; a.seed = p->last_seed; a.iter = p->last_iter; a.hard = p->last_hard;
+    a.tape = p->tape; a.grad = grad; a.dropped = p->dropped;
+    const int lanes = lanes_for(p, N, true);
+    return timed(p, STAMP_K_ROLLOUT_ADJ,
+                 [&] { return stamp::launch_rollout_adj(p->sc, a, lanes, p->stream); });
+}
+
+stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, float* m, float* v,
+                  int step, float lr, int sgd_phase, float* h_out, float* phi_out) {
+    const int D = p->sc.D;
+    const float* dir = grad;
+    if (!sgd_phase) {
+        stamp::SvgdScratch s{p->d2, p->hist, p->h, p->phi, p->flag};
+        float* phi = phi_out ? phi_out : p->phi;
+        STAMP_CUDA(cudaMemsetAsync(p->hist, 0, (2048 + 2048 + 1024) * sizeof(unsigned), p->stream));
+        STAMP_TRY(timed(p, STAMP_K_PAIRWISE,
+                        [&] { return stamp::launch_pairwise(theta, N, D, s, p->stream); }));
+        if (N >= 2)
+            for (int dg = 1; dg <= 2; ++dg)
+                STAMP_TRY(timed(p, STAMP_K_MEDIAN,
+                                [&] { return stamp::launch_median_digit(N, dg, s, p->stream); }));
+        STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
+            return stamp::launch_phi(theta, grad, N, D, s, phi, h_out, p->stream);
+        }));
+        dir = phi;
+    } else {
+        if (phi_out)
+            STAMP_CUDA(cudaMemcpyAsync(phi_out, grad, (size_t)N * D * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, p->stream));
+        if (h_out)
+            STAMP_CUDA(cudaMemcpyAsync(h_out, p->one, sizeof(float), cudaMemcpyDeviceToDevice,
+                                       p->stream));
+    }
+    return timed(p, STAMP_K_ADAM, [&] {
+        return stamp::launch_adam(theta, dir, m, v, N * D, step, lr, p->flag, p->stream);
+    });
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+bool finite_nonneg(float x) { return std::isfinite(x) && x >= 0.f; }
+
+}  // namespace
+
+namespace stamp {
+
+bool lanes_supported(int nb, int lanes) {
+    switch (nb) {
+        case 1: return lanes == 1 || lanes == 2 || lanes == 4;
+        case 2: return lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16;
+        case 3: case 4: return lanes == 8 || lanes == 16 || lanes == 32;
+    }
+    return false;
+}
+
+int default_lanes(int nb, int N, bool adjoint) {
+    (void)N; (void)adjoint;
+    return nb == 1 ? 4 : nb == 2 ? 8 : 16;
+}
+
+cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st) {
+    switch (sc.nb) {
+        case 1: return launch_rollout_nb1(sc, a, lanes, false, st);
+        case 2: return launch_rollout_nb2(sc, a, lanes, false, st);
+        case 3: return launch_rollout_nb3(sc, a, lanes, false, st);
+        case 4: return launch_rollout_nb4(sc, a, lanes, false, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rollout_adj(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st) {
+    switch (sc.nb) {
+        case 1: return launch_rollout_nb1(sc, a, lanes, true, st);
+        case 2: return launch_rollout_nb2(sc, a, lanes, true, st);
+        case 3: return launch_rollout_nb3(sc, a, lanes, true, st);
+        case 4: return launch_rollout_nb4(sc, a, lanes, true, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace stamp
+
+extern "C" {
+
+const char* stamp_status_str(stamp_status s) {
+    switch (s) {
+        case STAMP_OK: return "ok";
+        case STAMP_EINVAL: return "invalid argument";
+        case STAMP_ENOMEM: return "out of memory";
+        case STAMP_ECUDA: return "CUDA error";
+        case STAMP_ENONFINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+const char* stamp_last_error(void) { return g_err.c_str(); }
+
+stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init_poses,
+                                  const float* goal_poses, int max_particles, void* cuda_stream,
+                                  stamp_problem** out) {
+    if (!out) return fail(STAMP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d || !init_poses || !goal_poses) return fail(STAMP_EINVAL, "NULL description or poses");
+    if (d->n_blocks < 1 || d->n_blocks > stamp::kMaxBlocks)
+        return fail(STAMP_EINVAL, "n_blocks=%d outside [1, %d]", d->n_blocks, stamp::kMaxBlocks);
+    if (d->H < 1 || d->H > stamp::kMaxH) return fail(STAMP_EINVAL, "H=%d outside [1, %d]", d->H, stamp::kMaxH);
+    if (d->T < 1 || d->ckpt_every < 1 || d->T % d->ckpt_every)
+        return fail(STAMP_EINVAL, "need T >= 1, ckpt_every >= 1 and T %% ckpt_every == 0");
+    if (max_particles < 1 || max_particles > kMaxParticles)
+        return fail(STAMP_EINVAL, "max_particles=%d outside [1, %d]", max_particles, kMaxParticles);
+    const float pos[] = {d->half_size, d->mass, d->pusher_r, d->eps_v, d->eps_w, d->eps_t, d->dt, d->tau};
+    for (float x : pos)
+        if (!finite_pos(x)) return fail(STAMP_EINVAL, "a size, mass, smoothing, dt or tau is not > 0");
+    const float nonneg[] = {d->mu, d->mu_c, d->g, d->k_contact, d->c_contact, d->w_yaw, d->w_push,
+                            d->offset_max, d->dist_max};
+    for (float x : nonneg)
+        if (!finite_nonneg(x)) return fail(STAMP_EINVAL, "a coefficient or range is negative or not finite");
+    for (int q = 0; q < 3 * d->n_blocks; ++q)
+        if (!std::isfinite(init_poses[q]) || !std::isfinite(goal_poses[q]))
+            return fail(STAMP_EINVAL, "non-finite pose");
+
+    stamp_problem* p = new stamp_problem();
+    SimConst& sc = p->sc;
+    std::memset(&sc, 0, sizeof sc);
+    sc.nb = d->n_blocks; sc.H = d->H; sc.T = d->T; sc.C = d->ckpt_every;
+    sc.M = 4 * sc.nb; sc.P = sc.M + 2; sc.D = sc.H * sc.P; sc.S = 6 * sc.nb;
+    sc.n_ckpt = sc.H * sc.T / sc.C;
+    const double a = 2.0 * d->half_size;
+    const double inertia = d->mass * (a * a + a * a) / 12.0;                   // uniform square
+    const double r_eff = a / 6.0 * (std::sqrt(2.0) + std::log(1.0 + std::sqrt(2.0)));
+    sc.hs = d->half_size; sc.r = d->pusher_r; sc.k = d->k_contact; sc.c = d->c_contact;
+    sc.mu_c = d->mu_c; sc.dt = d->dt; sc.inv_dt = (float)(1.0 / d->dt);
+    sc.inv_m = (float)(1.0 / d->mass); sc.inv_I = (float)(1.0 / inertia);
+    sc.fric_lin = (float)((double)d->mu * d->mass * d->g);
+    sc.fric_ang = (float)((double)d->mu * d->mass * d->g * r_eff);
+    sc.eps_v2 = d->eps_v * d->eps_v; sc.eps_w2 = d->eps_w * d->eps_w; sc.eps_t2 = d->eps_t * d->eps_t;
+    sc.inv_tau = (float)(1.0 / d->tau); sc.w_yaw = d->w_yaw; sc.w_push = d->w_push;
+    sc.off_max = d->offset_max; sc.dist_max = d->dist_max;
+    for (int b = 0; b < sc.nb; ++b)
+        for (int q = 0; q < 3; ++q) {
+            sc.init[b][q] = init_poses[3 * b + q];
+            sc.goal[b][q] = goal_poses[3 * b + q];
+        }
+    const int D = sc.D;
+    // a checkpoint segment must fit in shared memory for one team
+    if ((size_t)(sc.C * (sc.S / 2) + 1) * 8 > 200 * 1024) {
+        delete p;
+        return fail(STAMP_EINVAL, "ckpt_every=%d too large for on-chip segment replay", sc.C);
+    }
+    p->max_n = max_particles;
+    p->stream = (cudaStream_t)cuda_stream;
+
+    // carve the arena
+    const size_t n = (size_t)max_particles;
+    struct Part { void** dst; size_t bytes; };
+    const Part parts[] = {
+        {(void**)&p->tape, (size_t)(sc.n_ckpt + 1) * n * sc.S * sizeof(float)},
+        {(void**)&p->cost, n * sizeof(float)},
+        {(void**)&p->grad, n * D * sizeof(float)},
+        {(void**)&p->theta, n * D * sizeof(float)},
+        {(void**)&p->m, n * D * sizeof(float)},
+        {(void**)&p->v, n * D * sizeof(float)},
+        {(void**)&p->phi, n * D * sizeof(float)},
+        {(void**)&p->d2, n * n * sizeof(float)},
+        {(void**)&p->h, sizeof(float)},
+        {(void**)&p->one, sizeof(float)},
+        {(void**)&p->hist, (2048 + 2048 + 1024) * sizeof(unsigned)},
+        {(void**)&p->stats, kMaxStatsIters * sizeof(unsigned)},
+        {(void**)&p->flag, sizeof(int)},
+        {(void**)&p->topk, n * sizeof(int)},
+        {(void**)&p->dropped, sizeof(unsigned long long)},
+    };
+    size_t total = 0;
+    for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&p->arena, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(STAMP_ENOMEM, "cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
+    }
+    size_t off = 0;
+    for (const Part& q : parts) {
+        *q.dst = p->arena + off;
+        off += (q.bytes + 255) / 256 * 256;
+    }
+    const float one = 1.f;
+    e = cudaMemcpy(p->one, &one, sizeof one, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->dropped, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(p->arena);
+        delete p;
+        return fail(STAMP_ECUDA, "problem set-up failed: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return STAMP_OK;
+}
+
+void stamp_problem_destroy(stamp_problem* p) {
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    cudaFree(p->arena);
+    delete p;
+}
+
+stamp_status stamp_set_lanes(stamp_problem* p, int fwd_lanes, int adj_lanes) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    if ((fwd_lanes && !stamp::lanes_supported(p->sc.nb, fwd_lanes)) ||
+        (adj_lanes && !stamp::lanes_supported(p->sc.nb, adj_lanes)))
+        return fail(STAMP_EINVAL, "unsupported lane count for n_blocks=%d", p->sc.nb);
+    p->fwd_lanes = fwd_lanes;
+    p->adj_lanes = adj_lanes;
+    return STAMP_OK;
+}
+
+stamp_status stamp_rollout_fwd(stamp_problem* p, const float* theta, int N, unsigned long long seed,
+                               int iter, int hard, float* cost, float* final_state) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_n(p, N));
+    STAMP_TRY(check_dev(theta, "theta"));
+    STAMP_TRY(check_dev(cost, "cost"));
+    STAMP_TRY(check_dev(final_state, "final_state", true));
+    return fwd(p, theta, N, seed, iter, hard ? 1 : 0, cost, final_state, nullptr);
+}
+
+stamp_status stamp_rollout_adjoint(stamp_problem* p, const float* theta, int N,
+                                   unsigned long long seed, int iter, float* grad_logp) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_n(p, N));
+    STAMP_TRY(check_dev(theta, "theta"));
+    STAMP_TRY(check_dev(grad_logp, "grad_logp"));
+    if (!p->have_tape || N != p->last_n || seed != p->last_seed || iter != p->last_iter)
+        return fail(STAMP_EINVAL, "adjoint must follow stamp_rollout_fwd with the same N, seed and iter");
+    return adj(p, theta, N, grad_logp);
+}
+
+stamp_status stamp_read_tape(stamp_problem* p, int N, float* tape_out) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_dev(tape_out, "tape_out"));
+    if (!p->have_tape || N != p->last_n) return fail(STAMP_EINVAL, "no tape for N=%d", N);
+    STAMP_CUDA(cudaMemcpyAsync(tape_out, p->tape,
+                               (size_t)(p->sc.n_ckpt + 1) * N * p->sc.S * sizeof(float),
+                               cudaMemcpyDeviceToDevice, p->stream));
+    return STAMP_OK;
+}
+
+stamp_status stamp_svgd_step(stamp_problem* p, float* theta, const float* grad_logp, int N,
+                             float* adam_m, float* adam_v, int step, float lr, int sgd_phase,
+                             float* h_out, float* phi_out) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_n(p, N));
+    STAMP_TRY(check_dev(theta, "theta"));
+    STAMP_TRY(check_dev(grad_logp, "grad_logp"));
+    STAMP_TRY(check_dev(adam_m, "adam_m"));
+    STAMP_TRY(check_dev(adam_v, "adam_v"));
+    STAMP_TRY(check_dev(h_out, "h_out", true));
+    STAMP_TRY(check_dev(phi_out, "phi_out", true));
+    if (step < 1) return fail(STAMP_EINVAL, "step must be >= 1");
+    if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
+    return svgd(p, theta, grad_logp, N, adam_m, adam_v, step, lr, sgd_phase, h_out, phi_out);
+}
+
+stamp_status stamp_solve(stamp_problem* p, int N, int svgd_iters, int sgd_iters,
+                         unsigned long long seed, float lr, const float* theta_init,
+                         float* theta_out, float* cost_out, int k, int* topk_particle,
+                         float* stats_out) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_n(p, N));
+    if (svgd_iters < 0 || sgd_iters < 0) return fail(STAMP_EINVAL, "negative iteration count");
+    const long long iters = (long long)svgd_iters + sgd_iters;
+    if (stats_out && iters > kMaxStatsIters)
+        return fail(STAMP_EINVAL, "stats_out supports at most %lld iterations", kMaxStatsIters);
+    if (!theta_out) return fail(STAMP_EINVAL, "theta_out is NULL");
+    if (k < 0 || (k > 0 && !topk_particle)) return fail(STAMP_EINVAL, "bad k / topk_particle");
+    if (k > 0 && N > stamp::kMaxTopkN) return fail(STAMP_EINVAL, "top-k needs N <= %d", stamp::kMaxTopkN);
+    if (k > N) return fail(STAMP_EINVAL, "k=%d > N=%d", k, N);
+    if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
+    const int D = p->sc.D;
+    const size_t nd = (size_t)N * D;
+    const bool out_dev = is_device_ptr(theta_out);
+    float* th = out_dev ? theta_out : p->theta;
+    if (theta_init)
+        STAMP_CUDA(cudaMemcpyAsync(th, theta_init, nd * sizeof(float), cudaMemcpyDefault, p->stream));
+    else
+        STAMP_TRY(timed(p, STAMP_K_INIT, [&] { return stamp::launch_init_theta(th, N, D, seed, p->stream); }));
+    STAMP_CUDA(cudaMemsetAsync(p->m, 0, nd * sizeof(float), p->stream));
+    STAMP_CUDA(cudaMemsetAsync(p->v, 0, nd * sizeof(float), p->stream));
+    if (stats_out) STAMP_CUDA(cudaMemsetAsync(p->stats, 0xFF, iters * sizeof(unsigned), p->stream));
+    for (long long it = 0; it < iters; ++it) {
+        STAMP_TRY(fwd(p, th, N, seed, (int)it, 0, p->cost, nullptr, stats_out ? p->stats + it : nullptr));
+        STAMP_TRY(adj(p, th, N, p->grad));
+        STAMP_TRY(svgd(p, th, p->grad, N, p->m, p->v, (int)it + 1, lr, it >= svgd_iters ? 1 : 0,
+                       nullptr, nullptr));
+    }
+    // hard evaluation (Gamma, no noise) and the distinct-plan top-k
+    float* ch = (cost_out && is_device_ptr(cost_out)) ? cost_out : p->cost;
+    STAMP_TRY(fwd(p, th, N, seed, -1, 1, ch, nullptr, nullptr));
+    if (k > 0)
+        STAMP_TRY(timed(p, STAMP_K_TOPK, [&] { return stamp::launch_topk(th, ch, N, p->sc, k, p->topk, p->stream); }));
+    if (!out_dev)
+        STAMP_CUDA(cudaMemcpyAsync(theta_out, th, nd * sizeof(float), cudaMemcpyDefault, p->stream));
+    if (cost_out && ch != cost_out)
+        STAMP_CUDA(cudaMemcpyAsync(cost_out, ch, N * sizeof(float), cudaMemcpyDefault, p->stream));
+    if (k > 0)
+        STAMP_CUDA(cudaMemcpyAsync(topk_particle, p->topk, k * sizeof(int), cudaMemcpyDefault, p->stream));
+    if (stats_out)
+        STAMP_CUDA(cudaMemcpyAsync(stats_out, p->stats, iters * sizeof(float), cudaMemcpyDefault, p->stream));
+    STAMP_CUDA(cudaStreamSynchronize(p->stream));
+    STAMP_TRY(collect(p));
+    return check_flag(p);
+}
+
+stamp_status stamp_sync(stamp_problem* p) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_CUDA(cudaStreamSynchronize(p->stream));
+    STAMP_TRY(collect(p));
+    return check_flag(p);
+}
+
+stamp_status stamp_dropped_gradients(stamp_problem* p, long long* count) {
+    if (!p || !count) return fail(STAMP_EINVAL, "NULL problem or count");
+    STAMP_CUDA(cudaStreamSynchronize(p->stream));
+    unsigned long long n = 0;
+    STAMP_CUDA(cudaMemcpy(&n, p->dropped, sizeof n, cudaMemcpyDeviceToHost));
+    *count = (long long)n;
+    return STAMP_OK;
+}
+
+stamp_status stamp_set_profiling(stamp_problem* p, int enable) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_CUDA(cudaStreamSynchronize(p->stream));
+    p->ev_used = 0;
+    for (int q = 0; q < STAMP_NKERNELS; ++q) { p->ms[q] = 0.0; p->launches[q] = 0; }
+    p->prof = enable != 0;
+    if (p->prof && p->ev.empty()) {
+        constexpr size_t kPairs = 1 << 15;
+        p->ev.resize(2 * kPairs);
+        for (cudaEvent_t& e : p->ev) STAMP_CUDA(cudaEventCreate(&e));
+        p->ev_kind.resize(kPairs);
+    }
+    return STAMP_OK;
+}
+
+stamp_status stamp_get_kernel_times(stamp_problem* p, double* ms_out, long long* launches_out) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    for (int q = 0; q < STAMP_NKERNELS; ++q) {
+        if (ms_out) ms_out[q] = p->ms[q];
+        if (launches_out) launches_out[q] = p->launches[q];
+    }
+    return STAMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Internal declarations of the STAMP CUDA library (sm_103a).
+//
+// The hot path is one Stein iteration of Algorithm 1 over N relaxed pushing
+// plans: forward rollout (Sec. III-B), checkpointed adjoint, pairwise
+// distances + median bandwidth, Stein direction (Eq. svgd) and Adam.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace stamp {
+
+constexpr int kMaxBlocks = 4;     // n_blocks <= 4  ->  M = 4*n_blocks <= 16 choices
+constexpr int kMaxH = 16;         // plan codes pack 4 bits per action into 64 bits
+constexpr int kMaxTopkN = 8192;   // single-CTA bitonic sort of (cost, index)
+
+// Problem constants in the form the kernels use (derived once on the host).
+struct SimConst {
+    int nb, H, T, C, M, P, D, S, n_ckpt;   // n_ckpt = H*T/C
+    float hs, r, k, c, mu_c, dt, inv_dt, inv_m, inv_I;
+    float fric_lin;      // mu*m*g            (ground friction force scale)
+    float fric_ang;      // mu*m*g*r_eff      (ground friction torque scale)
+    float eps_v2, eps_w2, eps_t2;
+    float inv_tau, w_yaw, w_push, off_max, dist_max;
+    float init[kMaxBlocks][3];
+    float goal[kMaxBlocks][3];
+};
+
+struct RolloutArgs {
+    const float* theta;     // N x D
+    int N;
+    uint64_t seed;
+    int iter;               // < 0: no Gumbel noise
+    int hard;               // 1: one-hot argmax weights
+    float* tape;            // (n_ckpt + 1) x N x S
+    float* cost;            // N (forward) or NULL
+    float* final_state;     // N x S or NULL
+    unsigned* stats_min;    // one word, atomicMin of cost bits, or NULL
+    float* grad;            // N x D (adjoint): grad log rho = -dC/dtheta
+    unsigned long long* dropped;   // count of particles whose reverse sweep overflowed
+};
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator: output
+// number ctr+1 of the generator started at state `key` is mix(key+(ctr+1)*G).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64(uint64_t key, uint64_t ctr) {
+    return sm_mix(key + (ctr + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+// Top 23 bits as a float in (0,1): ((x>>41)+0.5)/2^23, exact in float32.
+__host__ __device__ __forceinline__ float u23(uint64_t x) {
+    return ((float)(x >> 41) + 0.5f) * 1.1920928955078125e-7f;
+}
+constexpr uint64_t kStreamGumbel = 0, kStreamInit = 1;
+
+// Launchers (return the launch error).  `lanes` = threads cooperating on one
+// particle in the rollout kernels.
+cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st);
+cudaError_t launch_rollout_adj(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st);
+bool lanes_supported(int nb, int lanes);
+int default_lanes(int nb, int N, bool adjoint);
+
+// Per-NB launchers defined in rollout_nb*.cu.
+cudaError_t launch_rollout_nb1(const SimConst&, const RolloutArgs&, int, bool, cudaStream_t);
+cudaError_t launch_rollout_nb2(const SimConst&, const RolloutArgs&, int, bool, cudaStream_t);
+cudaError_t launch_rollout_nb3(const SimConst&, const RolloutArgs&, int, bool, cudaStream_t);
+cudaError_t launch_rollout_nb4(const SimConst&, const RolloutArgs&, int, bool, cudaStream_t);
+
+// SVGD step pieces (svgd.cu).  Scratch buffers are owned by the problem.
+struct SvgdScratch {
+    float* d2;            // N x N squared distances
+    unsigned* hist;       // 2048 + 2048 + 1024 radix-select counters
+    float* h;             // bandwidth (device scalar)
+    float* phi;           // N x D
+    int* flag;            // non-finite flag
+};
+cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch& s, cudaStream_t st);
+cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, cudaStream_t st);
+cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
+                       float* phi, float* h_out, cudaStream_t st);
+cudaError_t launch_adam(float* theta, const float* phi, float* m, float* v, int n_elems, int step,
+                        float lr, int* flag, cudaStream_t st);
+cudaError_t launch_init_theta(float* theta, int N, int D, uint64_t seed, cudaStream_t st);
+cudaError_t launch_topk(const float* theta, const float* cost, int N, const SimConst& sc, int k,
+                        int* topk_out, cudaStream_t st);
+
+}  // namespace stamp

@@ -1,0 +1,229 @@
+"""ctypes binding of the STAMP C ABI (include/stamp.h).
+
+Argument marshalling only: every step of the hot path runs in libstamp.so's
+CUDA kernels.  Importing this module raises ImportError when the library has
+not been built (there is no CPU fallback).
+
+Pointer arguments accept a torch tensor (its data_ptr; float32/int32,
+contiguous), a numpy array (host memory) or a raw integer address.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstamp.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build() "
+                      "(python paper_2310_01775_gb300/build.py)")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+STAMP_OK, STAMP_EINVAL, STAMP_ENOMEM, STAMP_ECUDA, STAMP_ENONFINITE = range(5)
+KERNELS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init")
+STAMP_NKERNELS = len(KERNELS)
+
+
+class StampError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.stamp_status_str(status).decode()}: {msg}")
+        self.status = status
+
+
+class stamp_problem_desc(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int), ("H", ctypes.c_int), ("T", ctypes.c_int),
+                ("ckpt_every", ctypes.c_int)] + [
+        (n, ctypes.c_float) for n in (
+            "half_size", "mass", "mu", "mu_c", "g", "pusher_r", "k_contact", "c_contact",
+            "eps_v", "eps_w", "eps_t", "dt", "tau", "w_yaw", "w_push", "offset_max", "dist_max")]
+
+    @classmethod
+    def from_params(cls, p: dict) -> "stamp_problem_desc":
+        return cls(**{n: p[n] for n, _ in cls._fields_})
+
+
+_vp, _i, _ull, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float
+_sigs = {
+    "stamp_problem_create": [ctypes.POINTER(stamp_problem_desc), _vp, _vp, _i, _vp,
+                             ctypes.POINTER(_vp)],
+    "stamp_rollout_fwd": [_vp, _vp, _i, _ull, _i, _i, _vp, _vp],
+    "stamp_rollout_adjoint": [_vp, _vp, _i, _ull, _i, _vp],
+    "stamp_read_tape": [_vp, _i, _vp],
+    "stamp_svgd_step": [_vp, _vp, _vp, _i, _vp, _vp, _i, _f, _i, _vp, _vp],
+    "stamp_solve": [_vp, _i, _i, _i, _ull, _f, _vp, _vp, _vp, _i, _vp, _vp],
+    "stamp_sync": [_vp],
+    "stamp_set_profiling": [_vp, _i],
+    "stamp_get_kernel_times": [_vp, _vp, _vp],
+    "stamp_set_lanes": [_vp, _i, _i],
+    "stamp_dropped_gradients": [_vp, _vp],
+}
+for _name, _args in _sigs.items():
+    getattr(_lib, _name).argtypes = _args
+    getattr(_lib, _name).restype = ctypes.c_int
+_lib.stamp_problem_destroy.argtypes = [_vp]
+_lib.stamp_problem_destroy.restype = None
+_lib.stamp_status_str.argtypes = [ctypes.c_int]
+_lib.stamp_status_str.restype = ctypes.c_char_p
+_lib.stamp_last_error.restype = ctypes.c_char_p
+
+
+def _check(status: int) -> None:
+    if status != STAMP_OK:
+        raise StampError(status, _lib.stamp_last_error().decode())
+
+
+def _ptr(x):
+    """Address of a tensor / numpy array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arguments must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _f32(x, name):
+    if x is not None and hasattr(x, "dtype") and str(x.dtype) not in ("torch.float32", "float32"):
+        raise TypeError(f"{name} must be float32")
+    return _ptr(x)
+
+
+def stamp_problem_create(desc: stamp_problem_desc, init_poses, goal_poses, max_particles: int,
+                         cuda_stream: int | None = None) -> int:
+    init = np.ascontiguousarray(init_poses, dtype=np.float32)
+    goal = np.ascontiguousarray(goal_poses, dtype=np.float32)
+    out = _vp()
+    _check(_lib.stamp_problem_create(ctypes.byref(desc), init.ctypes.data, goal.ctypes.data,
+                                     max_particles, cuda_stream, ctypes.byref(out)))
+    return out.value
+
+
+def stamp_problem_destroy(prob: int) -> None:
+    _lib.stamp_problem_destroy(prob)
+
+
+def stamp_rollout_fwd(prob, theta, N, seed, iter, hard, cost, final_state=None):
+    _check(_lib.stamp_rollout_fwd(prob, _f32(theta, "theta"), N, seed, iter, int(hard),
+                                  _f32(cost, "cost"), _f32(final_state, "final_state")))
+
+
+def stamp_rollout_adjoint(prob, theta, N, seed, iter, grad_logp):
+    _check(_lib.stamp_rollout_adjoint(prob, _f32(theta, "theta"), N, seed, iter,
+                                      _f32(grad_logp, "grad_logp")))
+
+
+def stamp_read_tape(prob, N, tape_out):
+    _check(_lib.stamp_read_tape(prob, N, _f32(tape_out, "tape_out")))
+
+
+def stamp_svgd_step(prob, theta, grad_logp, N, adam_m, adam_v, step, lr, sgd_phase=0,
+                    h_out=None, phi_out=None):
+    _check(_lib.stamp_svgd_step(prob, _f32(theta, "theta"), _f32(grad_logp, "grad_logp"), N,
+                                _f32(adam_m, "adam_m"), _f32(adam_v, "adam_v"), step, lr,
+                                int(sgd_phase), _f32(h_out, "h_out"), _f32(phi_out, "phi_out")))
+
+
+def stamp_solve(prob, N, svgd_iters, sgd_iters, seed, lr, theta_init, theta_out, cost_out=None,
+                k=0, topk_particle=None, stats_out=None):
+    if topk_particle is not None and str(topk_particle.dtype) not in ("int32", "torch.int32"):
+        raise TypeError("topk_particle must be int32")
+    _check(_lib.stamp_solve(prob, N, svgd_iters, sgd_iters, seed, lr, _f32(theta_init, "theta_init"),
+                            _f32(theta_out, "theta_out"), _f32(cost_out, "cost_out"), k,
+                            _ptr(topk_particle), _f32(stats_out, "stats_out")))
+
+
+def stamp_sync(prob):
+    _check(_lib.stamp_sync(prob))
+
+
+def stamp_set_profiling(prob, enable: bool):
+    _check(_lib.stamp_set_profiling(prob, int(enable)))
+
+
+def stamp_get_kernel_times(prob) -> dict:
+    ms = np.zeros(STAMP_NKERNELS, dtype=np.float64)
+    n = np.zeros(STAMP_NKERNELS, dtype=np.int64)
+    _check(_lib.stamp_get_kernel_times(prob, ms.ctypes.data, n.ctypes.data))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+
+def stamp_set_lanes(prob, fwd_lanes: int, adj_lanes: int):
+    _check(_lib.stamp_set_lanes(prob, fwd_lanes, adj_lanes))
+
+
+def stamp_dropped_gradients(prob) -> int:
+    n = ctypes.c_longlong()
+    _check(_lib.stamp_dropped_gradients(prob, ctypes.byref(n)))
+    return n.value
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+class Problem:
+    """Owns a stamp_problem handle; methods forward to the functions above."""
+
+    def __init__(self, params: dict, init_poses, goal_poses, max_particles: int,
+                 cuda_stream: int | None = None):
+        self.params = dict(params)
+        self.M = 4 * params["n_blocks"]
+        self.P = self.M + 2
+        self.D = params["H"] * self.P
+        self.S = 6 * params["n_blocks"]
+        self.n_ckpt = params["H"] * params["T"] // params["ckpt_every"]
+        self.handle = stamp_problem_create(stamp_problem_desc.from_params(params), init_poses,
+                                           goal_poses, max_particles, cuda_stream)
+
+    def close(self):
+        if self.handle:
+            stamp_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rollout_fwd(self, theta, N, seed, iter, hard, cost, final_state=None):
+        stamp_rollout_fwd(self.handle, theta, N, seed, iter, hard, cost, final_state)
+
+    def rollout_adjoint(self, theta, N, seed, iter, grad_logp):
+        stamp_rollout_adjoint(self.handle, theta, N, seed, iter, grad_logp)
+
+    def read_tape(self, N, tape_out):
+        stamp_read_tape(self.handle, N, tape_out)
+
+    def svgd_step(self, theta, grad_logp, N, adam_m, adam_v, step, lr, sgd_phase=0, h_out=None,
+                  phi_out=None):
+        stamp_svgd_step(self.handle, theta, grad_logp, N, adam_m, adam_v, step, lr, sgd_phase,
+                        h_out, phi_out)
+
+    def solve(self, N, svgd_iters, sgd_iters, seed, lr, theta_init, theta_out, cost_out=None, k=0,
+              topk_particle=None, stats_out=None):
+        stamp_solve(self.handle, N, svgd_iters, sgd_iters, seed, lr, theta_init, theta_out,
+                    cost_out, k, topk_particle, stats_out)
+
+    def sync(self):
+        stamp_sync(self.handle)
+
+    def set_profiling(self, enable):
+        stamp_set_profiling(self.handle, enable)
+
+    def kernel_times(self):
+        return stamp_get_kernel_times(self.handle)
+
+    def set_lanes(self, fwd_lanes, adj_lanes):
+        stamp_set_lanes(self.handle, fwd_lanes, adj_lanes)
+
+    def dropped_gradients(self):
+        return stamp_dropped_gradients(self.handle)

@@ -1,0 +1,167 @@
+"""GPU rollout / adjoint parity against the FP64 oracle (through the C ABI).
+
+Tolerances: trajectories and costs within 1e-4 relative and gradients within
+1e-3 relative (max-norm per particle), on every particle whose rollout is
+well-conditioned at float32 rounding (see tests/_common.conditioned); the
+share of such particles is asserted too, so the bar cannot pass vacuously.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import stamp_oracle as O
+from paper_2310_01775_gb300 import workloads as W
+
+from _common import Reference, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(P):
+    """The problem as the library sees it: every constant rounded to float32."""
+    return {k: (float(np.float32(v)) if isinstance(v, float) else v) for k, v in P.items()}
+
+
+def setup(name, over, N, seed):
+    P = f32(W.params(name, **over))
+    init, goal = W.scene(P, seed)
+    init = init.astype(np.float32).astype(np.float64)
+    goal = goal.astype(np.float32).astype(np.float64)
+    M, _, D = O.dims(P)
+    theta = O.init_theta(seed, N, D).astype(np.float32)
+    return P, init, goal, M, D, theta
+
+
+def gpu_rollout(P, init, goal, theta, seed, it, lanes=None, hard=0):
+    from paper_2310_01775_gb300 import stamp as S
+    dev = torch.device("cuda:0")
+    N, D = theta.shape
+    prob = S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream)
+    if lanes:
+        prob.set_lanes(lanes, lanes)
+    th = torch.tensor(theta, device=dev)
+    cost = torch.empty(N, device=dev)
+    fin = torch.empty(N, prob.S, device=dev)
+    grad = torch.empty(N, D, device=dev)
+    tape = torch.empty(prob.n_ckpt + 1, N, prob.S, device=dev)
+    prob.rollout_fwd(th, N, seed, it, hard, cost, fin)
+    prob.read_tape(N, tape)
+    if not hard:
+        prob.rollout_adjoint(th, N, seed, it, grad)
+    prob.sync()
+    prob.close()
+    nb = P["n_blocks"]
+    tape = tape.cpu().numpy().transpose(1, 0, 2).reshape(N, -1, nb, 6)
+    return cost.cpu().numpy(), fin.cpu().numpy(), tape, grad.cpu().numpy()
+
+
+# Contact constants of the workloads (k=1e4, c=50) and a softer contact
+# (k=1e3, c=10) under which every particle is well-conditioned, so the bar
+# holds on all particles and over whole horizons.
+SOFT = dict(k_contact=1e3, c_contact=10.0)
+CASES = [
+    # name, overrides, N, lanes, minimum share of conditioned particles
+    ("pusher1_h2", dict(H=1, ckpt_every=1), 37, 1, 0.3),
+    ("pusher1_h2", dict(H=1, ckpt_every=1), 37, 2, 0.3),
+    ("pusher1_h2", dict(H=1, ckpt_every=1), 37, 4, 0.3),
+    ("pusher1_h4", dict(H=1, ckpt_every=1), 64, 4, 0.3),
+    ("pusher1_h2", dict(ckpt_every=1), 32, 4, 0.3),           # both actions, every substep
+    ("pusher1_h2", dict(ckpt_every=25), 33, 4, 0.3),          # checkpoint replay
+    ("pusher3_h6", dict(n_blocks=2, H=1, ckpt_every=1), 48, 8, 0.1),
+    ("pusher3_h6", dict(n_blocks=2, H=1, ckpt_every=25), 48, 16, 0.1),
+    ("pusher3_h6", dict(H=1, ckpt_every=1), 48, 16, 0.1),
+    ("pusher3_h6", dict(H=1, ckpt_every=25), 48, 8, 0.1),
+    ("pusher3_h6", dict(H=1, ckpt_every=20), 48, 32, 0.1),
+    ("pusher3_h6", dict(n_blocks=4, H=1, ckpt_every=25), 32, 16, 0.05),
+    ("pusher1_h2", dict(SOFT, ckpt_every=1), 40, 4, 1.0),
+    ("pusher1_h4", dict(SOFT), 40, 4, 1.0),                    # 4 actions of 100 substeps
+    ("pusher1_h4", dict(SOFT), 40, 1, 1.0),
+    ("pusher3_h6", dict(SOFT, n_blocks=2, H=2), 24, 8, 0.6),
+    ("pusher3_h6", dict(SOFT, H=2), 24, 16, 0.6),
+]
+
+
+@pytest.mark.parametrize("name,over,N,lanes,min_frac", CASES)
+def test_rollout_and_adjoint_parity(name, over, N, lanes, min_frac):
+    seed, it = 5, 3
+    P, init, goal, M, D, theta = setup(name, over, N, seed)
+    cost, fin, tape, grad = gpu_rollout(P, init, goal, theta, seed, it, lanes)
+    gum = O.gumbel_noise(seed, it, N, P["H"], M)
+    ref = Reference(theta, P, init, goal, gum, C=P["ckpt_every"])
+    assert tape.shape == ref.traj.shape
+    ref.check(tape, fin, cost, grad, min_frac=min_frac)
+    assert np.isfinite(tape).all() and np.isfinite(grad).all()
+
+
+def test_hard_rollout_parity():
+    seed = 2
+    P, init, goal, M, D, theta = setup("pusher1_h2", dict(ckpt_every=1), 40, seed)
+    cost, fin, tape, _ = gpu_rollout(P, init, goal, theta, seed, -1, hard=1)
+    ref = Reference(theta, P, init, goal, None, need_grad=False, hard=True)
+    ref.check(tape, fin, cost)
+
+
+@pytest.mark.parametrize("N", [1, 2, 31, 33])
+def test_ragged_particle_counts(N):
+    seed, it = 9, 0
+    P, init, goal, M, D, theta = setup("pusher1_h2", dict(H=1, ckpt_every=1), N, seed)
+    cost, fin, tape, grad = gpu_rollout(P, init, goal, theta, seed, it)
+    gum = O.gumbel_noise(seed, it, N, P["H"], M)
+    ref = Reference(theta, P, init, goal, gum)
+    ref.check(tape, fin, cost, grad, min_frac=0.0)
+    assert np.isfinite(grad).all()
+
+
+def test_noise_free_and_deterministic():
+    seed = 4
+    P, init, goal, M, D, theta = setup("pusher1_h2", {}, 16, seed)
+    a = gpu_rollout(P, init, goal, theta, seed, -1)
+    b = gpu_rollout(P, init, goal, theta, seed, -1)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    Reference(theta, P, init, goal, None, C=P["ckpt_every"]).check(a[2], a[1], a[0], a[3])
+
+
+@pytest.mark.parametrize("name,sample", [("pusher1_h4", 16), ("pusher3_h6", 12)])
+def test_full_size_sampled_particles(name, sample):
+    """Full workload in the default launch configuration; the oracle checks a
+    sample of particles one by one over the whole horizon."""
+    P = f32(W.params(name))
+    N, seed, it = P["N"], 11, 7
+    init, goal = W.scene(P, seed)
+    init = init.astype(np.float32).astype(np.float64)
+    goal = goal.astype(np.float32).astype(np.float64)
+    M, _, D = O.dims(P)
+    theta = O.init_theta(seed, N, D).astype(np.float32)
+    cost, fin, tape, grad = gpu_rollout(P, init, goal, theta, seed, it)
+    assert np.isfinite(cost).all() and np.isfinite(grad).all()
+    idx = np.random.default_rng(0).choice(N, size=sample, replace=False)
+    gum = O.gumbel_noise(seed, it, N, P["H"], M)[idx]
+    C, T, Pn = P["ckpt_every"], P["T"], M + 2
+    # over the first action (checkpoints up to substep T) ...
+    first = Reference(theta[idx][:, :Pn], dict(P, H=1), init, goal, gum[:, :1], C=C,
+                      need_grad=False)
+    first.check(tape[idx][:, : T // C + 1], tape[idx][:, T // C], None, min_frac=0.2)
+    # ... and over the whole horizon, where chaos leaves fewer conditioned particles
+    whole = Reference(theta[idx], P, init, goal, gum, C=C)
+    whole.check(tape[idx], fin[idx], cost[idx], grad[idx], min_frac=0.0)
+
+
+def test_adjoint_requires_matching_forward():
+    from paper_2310_01775_gb300 import stamp as S
+    seed = 1
+    P, init, goal, M, D, theta = setup("pusher1_h2", {}, 8, seed)
+    prob = S.Problem(P, init, goal, 8, torch.cuda.current_stream().cuda_stream)
+    th = torch.tensor(theta, device="cuda")
+    g = torch.empty(8, D, device="cuda")
+    c = torch.empty(8, device="cuda")
+    with pytest.raises(S.StampError):
+        prob.rollout_adjoint(th, 8, seed, 0, g)          # no forward yet
+    prob.rollout_fwd(th, 8, seed, 0, 0, c)
+    with pytest.raises(S.StampError):
+        prob.rollout_adjoint(th, 8, seed + 1, 0, g)      # other noise
+    with pytest.raises(S.StampError):
+        prob.rollout_fwd(th, 9, seed, 0, 0, c)           # N above max_particles
+    with pytest.raises(S.StampError):
+        prob.rollout_fwd(th.cpu(), 8, seed, 0, 0, c)     # host theta
+    prob.close()

@@ -26,9 +26,9 @@ def test_splitmix64_reference_outputs():
     assert got == vals
 
 
-def test_uniform24_range_and_mean():
+def test_uniform23_range_and_mean():
     x = O.sm64(O.sm64(7, 0), np.arange(200000, dtype=np.uint64))
-    u = O.uniform24(x)
+    u = O.uniform23(x)
     assert u.min() > 0.0 and u.max() < 1.0
     assert abs(u.mean() - 0.5) < 4 * math.sqrt(1 / 12 / u.size)
 
