@@ -41,7 +41,8 @@ typedef enum {
     STAMP_EINVAL = 1,      /* bad argument (null, size out of range, wrong pointer kind) */
     STAMP_ENOMEM = 2,      /* allocation failed in stamp_problem_create */
     STAMP_ECUDA = 3,       /* a CUDA runtime call failed; see stamp_last_error() */
-    STAMP_ENONFINITE = 4   /* a NaN/Inf cost, gradient or particle was produced */
+    STAMP_ENONFINITE = 4,  /* a NaN/Inf cost, gradient or particle was produced */
+    STAMP_ETIMEOUT = 5     /* a bounded device-side wait on an asynchronous copy gave up */
 } stamp_status;
 
 typedef struct stamp_problem stamp_problem;   /* opaque, owned by the library */
@@ -131,6 +132,7 @@ stamp_status stamp_read_tape(stamp_problem* prob, int N, float* tape_out);
  * Then one bias-corrected Adam step (Kingma & Ba 2015; beta 0.9/0.999,
  * eps 1e-8) with gradient -phi:
  *   theta: device N x D, updated in place.   grad_logp: device N x D.
+ *     Both 16-byte aligned (their row tiles are streamed by TMA bulk copies).
  *   adam_m, adam_v: device N x D moments, updated in place (zero at step 1).
  *   step: Adam step number, >= 1.   lr: step size.
  *   h_out: device float or NULL, receives h (1 in the SGD phase).

@@ -89,14 +89,10 @@ __device__ __forceinline__ void team_sum(Blocks<NB>& b) {
     team_sum<L>(b.vx); team_sum<L>(b.vy); team_sum<L>(b.om);
 }
 
-// sin/cos of a yaw: Cody-Waite reduction by 2*pi (two-part constant) to
-// [-pi, pi], where the hardware approximation's absolute error is below 2^-21.
-__device__ __forceinline__ void yaw_sincos(float x, float* s, float* c) {
-    const float q = rintf(x * 0.159154943091895336f);      // x / (2 pi)
-    float r = fmaf(-q, 6.28318548202514648f, x);           // float(2 pi)
-    r = fmaf(-q, -1.74845553e-7f, r);                      // 2 pi - float(2 pi)
-    __sincosf(r, s, c);
-}
+// sin/cos of a yaw (full-accuracy sincosf: the hardware approximation's
+// ~4e-7 absolute error measurably degrades parity through the contact
+// dynamics).
+__device__ __forceinline__ void yaw_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
 
 __device__ __forceinline__ void side_normal(int s, float& nx, float& ny) {
     nx = (s == 1) ? 1.f : (s == 3) ? -1.f : 0.f;

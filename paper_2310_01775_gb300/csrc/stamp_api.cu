@@ -55,7 +55,7 @@ struct stamp_problem {
     char* arena = nullptr;
     float *tape = nullptr, *cost = nullptr, *grad = nullptr, *theta = nullptr, *m = nullptr,
           *v = nullptr, *phi = nullptr, *d2 = nullptr, *h = nullptr, *one = nullptr;
-    unsigned *hist = nullptr, *stats = nullptr;
+    unsigned *hist = nullptr, *stats = nullptr, *sel = nullptr, *counter = nullptr;
     int *flag = nullptr, *topk = nullptr;
     unsigned long long* dropped = nullptr;
     // last forward
@@ -105,6 +105,7 @@ stamp_status check_flag(stamp_problem* p) {
     STAMP_CUDA(cudaMemcpy(&f, p->flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (f) {
         STAMP_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
+        if (f & 2) return fail(STAMP_ETIMEOUT, "a bounded device wait gave up (copy never completed)");
         return fail(STAMP_ENONFINITE, "a non-finite particle or Stein direction was produced");
     }
     return STAMP_OK;
@@ -160,17 +161,22 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
     const int D = p->sc.D;
     const float* dir = grad;
     if (!sgd_phase) {
-        stamp::SvgdScratch s{p->d2, p->hist, p->h, p->phi, p->flag};
+        stamp::SvgdScratch s{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
         float* phi = phi_out ? phi_out : p->phi;
         STAMP_CUDA(cudaMemsetAsync(p->hist, 0, (2048 + 2048 + 1024) * sizeof(unsigned), p->stream));
         STAMP_TRY(timed(p, STAMP_K_PAIRWISE,
                         [&] { return stamp::launch_pairwise(theta, N, D, s, p->stream); }));
-        if (N >= 2)
+        if (N >= 2) {
             for (int dg = 1; dg <= 2; ++dg)
-                STAMP_TRY(timed(p, STAMP_K_MEDIAN,
-                                [&] { return stamp::launch_median_digit(N, dg, s, p->stream); }));
+                STAMP_TRY(timed(p, STAMP_K_MEDIAN, [&] {
+                    return stamp::launch_median_digit(N, dg, s, dg == 2 ? h_out : nullptr, p->stream);
+                }));
+        } else if (h_out) {
+            STAMP_CUDA(cudaMemcpyAsync(h_out, p->one, sizeof(float), cudaMemcpyDeviceToDevice,
+                                       p->stream));
+        }
         STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
-            return stamp::launch_phi(theta, grad, N, D, s, phi, h_out, p->stream);
+            return stamp::launch_phi(theta, grad, N, D, s, phi, p->stream);
         }));
         dir = phi;
     } else {
@@ -202,9 +208,13 @@ bool lanes_supported(int nb, int lanes) {
     return false;
 }
 
+// Lanes per particle, from sweeps on GB300 (one block: 4/4; three blocks:
+// forward 32, adjoint 16).
 int default_lanes(int nb, int N, bool adjoint) {
-    (void)N; (void)adjoint;
-    return nb == 1 ? 4 : nb == 2 ? 8 : 16;
+    (void)N;
+    if (nb == 1) return 4;
+    if (nb == 2) return 8;
+    return adjoint ? 16 : 32;
 }
 
 cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st) {
@@ -238,6 +248,7 @@ const char* stamp_status_str(stamp_status s) {
         case STAMP_ENOMEM: return "out of memory";
         case STAMP_ECUDA: return "CUDA error";
         case STAMP_ENONFINITE: return "non-finite value";
+        case STAMP_ETIMEOUT: return "device wait timed out";
     }
     return "unknown status";
 }
@@ -318,6 +329,8 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         {(void**)&p->flag, sizeof(int)},
         {(void**)&p->topk, n * sizeof(int)},
         {(void**)&p->dropped, sizeof(unsigned long long)},
+        {(void**)&p->sel, 4 * sizeof(unsigned)},
+        {(void**)&p->counter, 3 * sizeof(unsigned)},
     };
     size_t total = 0;
     for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
@@ -336,6 +349,7 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
     e = cudaMemcpy(p->one, &one, sizeof one, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->dropped, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(p->counter, 0, 3 * sizeof(unsigned));
     if (e != cudaSuccess) {
         cudaFree(p->arena);
         delete p;
@@ -406,6 +420,8 @@ stamp_status stamp_svgd_step(stamp_problem* p, float* theta, const float* grad_l
     STAMP_TRY(check_dev(h_out, "h_out", true));
     STAMP_TRY(check_dev(phi_out, "phi_out", true));
     if (step < 1) return fail(STAMP_EINVAL, "step must be >= 1");
+    if ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(grad_logp)) & 15u)
+        return fail(STAMP_EINVAL, "theta and grad_logp must be 16-byte aligned");
     if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
     return svgd(p, theta, grad_logp, N, adam_m, adam_v, step, lr, sgd_phase, h_out, phi_out);
 }

@@ -74,15 +74,17 @@ cudaError_t launch_rollout_nb4(const SimConst&, const RolloutArgs&, int, bool, c
 // SVGD step pieces (svgd.cu).  Scratch buffers are owned by the problem.
 struct SvgdScratch {
     float* d2;            // N x N squared distances
-    unsigned* hist;       // 2048 + 2048 + 1024 radix-select counters
+    unsigned* hist;       // 2048 + 2048 + 1024 radix-select counters (zeroed per step)
+    unsigned* sel;        // digit 0 and its inner rank, digit 1 and its inner rank
+    unsigned* counter;    // 3 "last CTA" counters (zero between launches)
     float* h;             // bandwidth (device scalar)
-    float* phi;           // N x D
-    int* flag;            // non-finite flag
+    int* err;             // device error flags: 1 non-finite, 2 a bounded wait gave up
 };
 cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch& s, cudaStream_t st);
-cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, cudaStream_t st);
+cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h_out,
+                                cudaStream_t st);
 cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
-                       float* phi, float* h_out, cudaStream_t st);
+                       float* phi, cudaStream_t st);
 cudaError_t launch_adam(float* theta, const float* phi, float* m, float* v, int n_elems, int step,
                         float lr, int* flag, cudaStream_t st);
 cudaError_t launch_init_theta(float* theta, int N, int D, uint64_t seed, cudaStream_t st);

@@ -3,11 +3,12 @@
 //
 // Bandwidth: h = med/ln(N+1), med the lower median (rank floor((M-1)/2)) of
 // the M = N(N-1)/2 squared distances d2_ij, i<j -- the median heuristic the
-// paper uses for its RBF kernels (App. C.3).  It is selected exactly with a
+// paper uses for its RBF kernels (App. C.3).  It is selected exactly by a
 // three-digit radix select on the float bits (11 + 11 + 10 bits; the bits of
-// non-negative floats order like the floats), over a d2 matrix kept in HBM
-// (16 MB at N = 2048, L2-resident).  Every digit is picked by each CTA of the
-// next kernel from the previous histogram, so no kernel waits on another CTA.
+// non-negative floats order like the floats) over the d2 matrix, which stays
+// in L2 (4 MB at N = 1024).  Each pass histograms one digit; the last CTA of
+// the pass to finish (a device-scope counter, no waiting) picks the digit for
+// the next pass, and the last pass writes h.
 #include <cfloat>
 #include <cstdint>
 
@@ -16,23 +17,92 @@
 namespace stamp {
 namespace {
 
-constexpr int kTile = 32;     // pairwise tile edge
+constexpr int kTile = 32;                      // pairwise tile edge
 constexpr int kBins0 = 2048, kBins1 = 2048, kBins2 = 1024;
 
 __device__ __forceinline__ unsigned digit_of(unsigned bits, int d) {
     return d == 0 ? (bits >> 21) : d == 1 ? ((bits >> 10) & 2047u) : (bits & 1023u);
 }
 
-// d2 for one kTile x kTile tile of (i, j); histogram of digit 0 over i < j.
+// Bin of `hist` (256*PER bins) holding rank `rank`, and the rank inside it.
+// 256 threads; parallel prefix sum over the per-thread bin groups.
+template <int PER>
+__device__ void find_bin(const unsigned* hist, unsigned rank, unsigned& bin, unsigned& rem) {
+    __shared__ unsigned wsum[8];
+    __shared__ unsigned res[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned loc[PER], s = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        loc[q] = __ldcg(hist + tid * PER + q);
+        s += loc[q];
+    }
+    unsigned x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (tid == 0) { res[0] = 256 * PER - 1; res[1] = 0; }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = lane < 8 ? wsum[lane] : 0u, v = w;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < 8) wsum[lane] = v - w;      // exclusive prefix of the warps
+    }
+    __syncthreads();
+    const unsigned incl = x + wsum[warp], excl = incl - s;
+    if (excl <= rank && rank < incl) {
+        unsigned run = excl;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            if (run + loc[q] > rank) { res[0] = tid * PER + q; res[1] = rank - run; break; }
+            run += loc[q];
+        }
+    }
+    __syncthreads();
+    bin = res[0];
+    rem = res[1];
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned median_rank(int N) {
+    const unsigned long long m = (unsigned long long)N * (N - 1) / 2;
+    return (unsigned)((m - 1) / 2);
+}
+
+// True in exactly one thread block: the last of `total` to get here.
+__device__ bool last_block(unsigned* counter, unsigned total) {
+    __shared__ bool last;
+    __threadfence();            // this thread's histogram atomics are visible device-wide
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == total - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) *counter = 0u;   // ready for the next launch
+    return last;
+}
+
+// d2 for one upper-triangle tile pair (bi <= bj), mirrored into the lower
+// triangle; histogram of digit 0 over i < j.  The last CTA picks digit 0.
 __global__ void __launch_bounds__(256) pairwise_kernel(const float* __restrict__ theta, int N,
                                                        int D, float* __restrict__ d2,
-                                                       unsigned* __restrict__ hist) {
+                                                       unsigned* __restrict__ hist,
+                                                       unsigned* __restrict__ sel,
+                                                       unsigned* __restrict__ counter,
+                                                       float* __restrict__ h_dev) {
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi > bj) return;
     extern __shared__ float sm[];
-    const int ld = D + 1;                        // padded row: conflict-free column walks
+    const int ld = D + 1;                        // padded rows: conflict-free column walks
     float* A = sm;
     float* B = sm + kTile * ld;
     __shared__ unsigned h0[kBins0];
-    const int bi = blockIdx.y, bj = blockIdx.x;
+    __shared__ float tile[kTile][kTile + 1];
     const int i0 = bi * kTile, j0 = bj * kTile;
     for (int t = threadIdx.x; t < kBins0; t += blockDim.x) h0[t] = 0u;
     for (int t = threadIdx.x; t < kTile * D; t += blockDim.x) {
@@ -54,157 +124,245 @@ __global__ void __launch_bounds__(256) pairwise_kernel(const float* __restrict__
     const int i = i0 + r;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int j = j0 + c0 + 8 * q;
+        const int c = c0 + 8 * q, j = j0 + c;
+        tile[r][c] = acc[q];
         if (i < N && j < N) {
             d2[(size_t)i * N + j] = acc[q];
             if (i < j) atomicAdd(&h0[digit_of(__float_as_uint(acc[q]), 0)], 1u);
         }
     }
     __syncthreads();
+    if (bi != bj)   // mirror: coalesced rows of the lower triangle
+        for (int t = threadIdx.x; t < kTile * kTile; t += blockDim.x) {
+            const int rr = t / kTile, cc = t % kTile;   // rr indexes j, cc indexes i
+            if (j0 + rr < N && i0 + cc < N) d2[(size_t)(j0 + rr) * N + i0 + cc] = tile[cc][rr];
+        }
     for (int t = threadIdx.x; t < kBins0; t += blockDim.x)
         if (h0[t]) atomicAdd(&hist[t], h0[t]);
-}
-
-// Find the bin of `hist` (nbins) holding rank `rank`; returns the bin and the
-// rank inside it.  256 threads.
-__device__ void find_bin(const unsigned* hist, int nbins, unsigned rank, unsigned& bin,
-                         unsigned& rem) {
-    __shared__ unsigned part[256];
-    __shared__ unsigned res[2];
-    const int per = nbins / 256;
-    unsigned s = 0;
-    for (int q = 0; q < per; ++q) s += hist[threadIdx.x * per + q];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned run = 0;
-        int t = 0;
-        while (t < 255 && run + part[t] <= rank) run += part[t++];
-        int b = t * per;
-        for (int q = 0; q < per; ++q, ++b) {
-            const unsigned hb = hist[b];
-            if (run + hb > rank || q == per - 1) break;
-            run += hb;
+    const unsigned nt = gridDim.x;
+    if (last_block(counter, nt * (nt + 1) / 2)) {
+        if (N < 2) {
+            if (threadIdx.x == 0) *h_dev = 1.f;
+            return;
         }
-        res[0] = (unsigned)b;
-        res[1] = rank - run;
+        unsigned b0, r0;
+        find_bin<kBins0 / 256>(hist, median_rank(N), b0, r0);
+        if (threadIdx.x == 0) { sel[0] = b0; sel[1] = r0; }
     }
-    __syncthreads();
-    bin = res[0];
-    rem = res[1];
-    __syncthreads();
-}
-
-__device__ __forceinline__ unsigned median_rank(int N) {
-    const unsigned long long m = (unsigned long long)N * (N - 1) / 2;
-    return (unsigned)((m - 1) / 2);
 }
 
 // Histogram of digit `dg` (1 or 2) over the i<j entries whose higher digits
-// match the prefix selected so far.
-__global__ void __launch_bounds__(256) median_digit_kernel(int N, int dg, const float* __restrict__ d2,
-                                                           unsigned* __restrict__ hist) {
+// match the prefix chosen so far; rows of the upper triangle, grid-strided.
+__global__ void __launch_bounds__(256) median_digit_kernel(int N, int dg,
+                                                           const float* __restrict__ d2,
+                                                           unsigned* __restrict__ hist,
+                                                           unsigned* __restrict__ sel,
+                                                           unsigned* __restrict__ counter,
+                                                           float* __restrict__ h_dev,
+                                                           float* __restrict__ h_out) {
     __shared__ unsigned hloc[kBins1];
-    unsigned b0, r0, b1 = 0, r1;
-    find_bin(hist, kBins0, median_rank(N), b0, r0);
-    if (dg == 2) find_bin(hist + kBins0, kBins1, r0, b1, r1);
+    const unsigned b0 = __ldcg(sel), b1 = dg == 2 ? __ldcg(sel + 2) : 0u;
+    const unsigned prefix = dg == 1 ? b0 : ((b0 << 11) | b1);
+    const int shift = dg == 1 ? 21 : 10;
     const int nb = dg == 1 ? kBins1 : kBins2;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) hloc[t] = 0u;
     __syncthreads();
-    const size_t total = (size_t)N * N;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / N), j = (int)(e % N);
-        if (j <= i) continue;
-        const unsigned bits = __float_as_uint(d2[e]);
-        const bool match = dg == 1 ? (bits >> 21) == b0 : (bits >> 10) == ((b0 << 11) | b1);
-        if (match) atomicAdd(&hloc[digit_of(bits, dg)], 1u);
+    for (int i = blockIdx.x; i < N - 1; i += gridDim.x) {
+        const float* row = d2 + (size_t)i * N;
+        for (int j = i + 1 + threadIdx.x; j < N; j += blockDim.x) {
+            const unsigned bits = __float_as_uint(row[j]);
+            if ((bits >> shift) == prefix) atomicAdd(&hloc[digit_of(bits, dg)], 1u);
+        }
     }
     __syncthreads();
     unsigned* out = hist + (dg == 1 ? kBins0 : kBins0 + kBins1);
     for (int t = threadIdx.x; t < nb; t += blockDim.x)
         if (hloc[t]) atomicAdd(&out[t], hloc[t]);
+    if (last_block(counter, gridDim.x)) {
+        if (dg == 1) {
+            unsigned b1n, r1;
+            find_bin<kBins1 / 256>(out, __ldcg(sel + 1), b1n, r1);
+            if (threadIdx.x == 0) { sel[2] = b1n; sel[3] = r1; }
+        } else {
+            unsigned b2, r2;
+            find_bin<kBins2 / 256>(out, __ldcg(sel + 3), b2, r2);
+            if (threadIdx.x == 0) {
+                const float med = __uint_as_float((b0 << 21) | (b1 << 10) | b2);
+                float h = med / logf((float)N + 1.f);
+                h = (h >= 1e-12f) ? h : 1.f;
+                *h_dev = h;
+                if (h_out) *h_out = h;
+            }
+        }
+    }
 }
 
-// h from the three digit histograms (each CTA recomputes it).
-__device__ float bandwidth(int N, const unsigned* hist) {
-    if (N < 2) return 1.f;
-    unsigned b0, r0, b1, r1, b2, r2;
-    find_bin(hist, kBins0, median_rank(N), b0, r0);
-    find_bin(hist + kBins0, kBins1, r0, b1, r1);
-    find_bin(hist + kBins0 + kBins1, kBins2, r1, b2, r2);
-    const float med = __uint_as_float((b0 << 21) | (b1 << 10) | b2);
-    const float h = med / logf((float)N + 1.f);
-    return (h >= 1e-12f) ? h : 1.f;
+// ---- TMA bulk copies and mbarriers (inline PTX) -----------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0),
+// completion counted on `bar` in bytes.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes,
+                                           uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+constexpr unsigned kWaitLimit = 1u << 20;   // bounded mbarrier waits (then error flag)
 
 // phi_i = (1/N) sum_j [k_ij g_j + (2/h) k_ij (theta_i - theta_j)], k_ij = exp(-d2_ij/h).
-constexpr int kRows = 8, kCols = 64;
-__global__ void __launch_bounds__(256) phi_kernel(const float* __restrict__ theta,
-                                                  const float* __restrict__ grad, int N, int D,
-                                                  const float* __restrict__ d2,
-                                                  const unsigned* __restrict__ hist,
-                                                  float* __restrict__ phi, float* h_dev,
-                                                  float* h_out) {
-    extern __shared__ float sm[];
-    float* Tj = sm;                       // kCols x D
-    float* Gj = Tj + kCols * D;           // kCols x D
-    float* Kij = Gj + kCols * D;          // kRows x kCols
-    float* Ti = Kij + kRows * kCols;      // kRows x D
-    const float h = bandwidth(N, hist);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (h_dev) *h_dev = h;
-        if (h_out) *h_out = h;
+// A warp owns kR rows; lane l owns columns l, l+32, ...  (DP slots).  The j
+// range is walked in tiles of kTJ rows of theta and grad, which are
+// contiguous in HBM: one thread streams each tile into one of two shared
+// memory stages with 1-D TMA bulk copies (mbarrier completion), one tile
+// ahead of the compute.  The d2 values of the next tile are prefetched into
+// registers; k_ij for the warp's rows is one float4 per j (a broadcast load).
+constexpr int kR = 4, kW = 2, kTJ = 32;
+__host__ __device__ constexpr int phi_stage_floats(int D, int DP) {
+    return ((kTJ * D + 32 * DP) + 3) / 4 * 4;   // per array, 16-byte multiple
+}
+template <int DP>
+__global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ theta,
+                                                      const float* __restrict__ grad, int N, int D,
+                                                      const float* __restrict__ d2,
+                                                      const float* __restrict__ h_dev,
+                                                      float* __restrict__ phi, int* err) {
+    extern __shared__ __align__(128) float sm[];
+    const int sf = phi_stage_floats(D, DP);
+    // stage s: theta tile at sm + 2*s*sf, grad tile right after it
+    float4* Ks = reinterpret_cast<float4*>(sm + 4 * sf);             // kW x kTJ
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Ks + kW * kTJ);       // 2 stages
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ib = (blockIdx.x * kW + warp) * kR;
+    const int ntiles = (N + kTJ - 1) / kTJ;
+    const float inv_h = 1.f / __ldcg(h_dev);
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_async_shared();
     }
-    const float inv_h = 1.f / h;
-    const int i0 = blockIdx.x * kRows;
-    const int nout = kRows * D;
-    for (int t = threadIdx.x; t < nout; t += blockDim.x) {
-        const int r = t / D, d = t % D;
-        Ti[t] = (i0 + r < N) ? theta[(size_t)(i0 + r) * D + d] : 0.f;
+    __syncthreads();
+    // thread 0 streams tile t into stage t&1: the 16-byte-aligned bulk of the
+    // contiguous rows by TMA, a ragged tail (< 16 bytes) by plain copies
+    auto issue = [&](int t) {
+        const int s = t & 1, j0 = t * kTJ, n = min(kTJ, N - j0) * D;
+        const unsigned bulk = (unsigned)(n * 4) & ~15u;
+        mbar_expect_tx(&bar[s], 2 * bulk);
+        float* Ts = sm + 2 * s * sf;
+        float* Gs = Ts + sf;
+        if (bulk) {
+            tma_load_1d(Ts, theta + (size_t)j0 * D, bulk, &bar[s]);
+            tma_load_1d(Gs, grad + (size_t)j0 * D, bulk, &bar[s]);
+        }
+        for (int f = bulk / 4; f < n; ++f) {
+            Ts[f] = theta[(size_t)j0 * D + f];
+            Gs[f] = grad[(size_t)j0 * D + f];
+        }
+    };
+    if (tid == 0) {
+        issue(0);
+        if (ntiles > 1) issue(1);
     }
-    constexpr int kMaxOut = 9;            // outputs per thread: kRows*D <= 9*256 (D <= 288)
-    float acc_a[kMaxOut], acc_r[kMaxOut];
+    float ti[kR][DP], ag[kR][DP], ar[kR][DP], dv[kR];
 #pragma unroll
-    for (int q = 0; q < kMaxOut; ++q) acc_a[q] = acc_r[q] = 0.f;
-    for (int j0 = 0; j0 < N; j0 += kCols) {
-        __syncthreads();
-        const int nj = min(kCols, N - j0);
-        for (int t = threadIdx.x; t < nj * D; t += blockDim.x) {
-            Tj[t] = theta[(size_t)j0 * D + t];
-            Gj[t] = grad[(size_t)j0 * D + t];
-        }
-        for (int t = threadIdx.x; t < kRows * kCols; t += blockDim.x) {
-            const int r = t / kCols, c = t % kCols;
-            const int i = i0 + r, j = j0 + c;
-            Kij[t] = (i < N && c < nj) ? expf(-d2[(size_t)i * N + j] * inv_h) : 0.f;
-        }
-        __syncthreads();
+    for (int r = 0; r < kR; ++r) {
 #pragma unroll
-        for (int q = 0; q < kMaxOut; ++q) {
-            const int o = threadIdx.x + q * 256;
-            if (o >= nout) break;
-            const int r = o / D, d = o % D;
-            const float ti = Ti[o];
-            float sa = acc_a[q], sr = acc_r[q];
-            for (int c = 0; c < nj; ++c) {
-                const float kk = Kij[r * kCols + c];
-                sa = fmaf(kk, Gj[c * D + d], sa);
-                sr = fmaf(kk, ti - Tj[c * D + d], sr);
+        for (int q = 0; q < DP; ++q) {
+            const int d = lane + 32 * q;
+            ti[r][q] = (ib + r < N && d < D) ? theta[(size_t)(ib + r) * D + d] : 0.f;
+            ag[r][q] = ar[r][q] = 0.f;
+        }
+        dv[r] = (ib + r < N && lane < N) ? d2[(size_t)(ib + r) * N + lane] : 0.f;
+    }
+    unsigned phases = 0u;                       // bit s: parity of stage s
+    for (int t = 0; t < ntiles; ++t) {
+        const int s = t & 1, j0 = t * kTJ, nj = min(kTJ, N - j0);
+        {
+            float kv[kR];
+#pragma unroll
+            for (int r = 0; r < kR; ++r) kv[r] = (ib + r < N && lane < nj) ? expf(-dv[r] * inv_h) : 0.f;
+            Ks[warp * kTJ + lane] = make_float4(kv[0], kv[1], kv[2], kv[3]);
+        }
+        if (t + 1 < ntiles) {   // next tile's distances, consumed one iteration later
+            const int jn = j0 + kTJ + lane;
+#pragma unroll
+            for (int r = 0; r < kR; ++r) dv[r] = (ib + r < N && jn < N) ? d2[(size_t)(ib + r) * N + jn] : 0.f;
+        }
+        const unsigned par = (phases >> s) & 1u;
+        unsigned spins = 0;
+        while (!mbar_try_wait(&bar[s], par) && ++spins < kWaitLimit) {
+        }
+        if (__syncthreads_or(spins >= kWaitLimit)) {   // a copy never landed: report, stop
+            if (tid == 0) {
+                atomicOr(err, 2);
+                // a last bounded wait for the copies still in flight (this
+                // stage and, if issued, the next) before the CTA exits
+                for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&bar[s], par); ++w) {
+                }
+                const unsigned pn = (phases >> (s ^ 1)) & 1u;
+                if (t + 1 < ntiles)
+                    for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&bar[s ^ 1], pn); ++w) {
+                    }
             }
-            acc_a[q] = sa;
-            acc_r[q] = sr;
+            return;
+        }
+        phases ^= 1u << s;
+        const float* Tj = sm + 2 * s * sf;
+        const float* Gj = Tj + sf;
+        for (int jj = 0; jj < nj; ++jj) {
+            const float4 k4 = Ks[warp * kTJ + jj];
+            const float kk[kR] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+            for (int q = 0; q < DP; ++q) {
+                const float g = Gj[jj * D + lane + 32 * q];
+                const float tv = Tj[jj * D + lane + 32 * q];
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    ag[r][q] = fmaf(kk[r], g, ag[r][q]);
+                    ar[r][q] = fmaf(kk[r], ti[r][q] - tv, ar[r][q]);
+                }
+            }
+        }
+        __syncthreads();                       // stage s and Ks fully read
+        if (tid == 0 && t + 2 < ntiles) {
+            fence_async_shared();
+            issue(t + 2);
         }
     }
-    const float inv_n = 1.f / (float)N;
+    const float inv_n = 1.f / (float)N, two_h = 2.f * inv_h;
 #pragma unroll
-    for (int q = 0; q < kMaxOut; ++q) {
-        const int o = threadIdx.x + q * 256;
-        if (o >= nout) break;
-        const int r = o / D, d = o % D;
-        if (i0 + r < N)
-            phi[(size_t)(i0 + r) * D + d] = (acc_a[q] + 2.f * inv_h * acc_r[q]) * inv_n;
-    }
+    for (int r = 0; r < kR; ++r)
+#pragma unroll
+        for (int q = 0; q < DP; ++q) {
+            const int d = lane + 32 * q;
+            if (ib + r < N && d < D)
+                phi[(size_t)(ib + r) * D + d] = (ag[r][q] + two_h * ar[r][q]) * inv_n;
+        }
 }
 
 // Adam (Kingma & Ba 2015) with gradient -phi; flags non-finite inputs/results.
@@ -283,6 +441,22 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ th
     }
 }
 
+template <int DP>
+cudaError_t phi_launch(const float* theta, const float* grad, int N, int D, const float* d2,
+                       const float* h_dev, float* phi, int* err, cudaStream_t st) {
+    const size_t smem = (size_t)4 * phi_stage_floats(D, DP) * sizeof(float) +
+                        (size_t)kW * kTJ * sizeof(float4) + 2 * sizeof(uint64_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(phi_kernel<DP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int rows = kW * kR;
+    phi_kernel<DP><<<(N + rows - 1) / rows, kW * 32, smem, st>>>(theta, grad, N, D, d2, h_dev, phi,
+                                                                 err);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch& s,
@@ -294,29 +468,35 @@ cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch&
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    pairwise_kernel<<<dim3(nt, nt), 256, smem, st>>>(theta, N, D, s.d2, s.hist);
+    pairwise_kernel<<<dim3(nt, nt), 256, smem, st>>>(theta, N, D, s.d2, s.hist, s.sel, s.counter,
+                                                     s.h);
     return cudaGetLastError();
 }
 
-cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, cudaStream_t st) {
-    const long long total = (long long)N * N;
-    int grid = (int)((total + 255) / 256);
-    if (grid > 152 * 8) grid = 152 * 8;
-    median_digit_kernel<<<grid, 256, 0, st>>>(N, digit, s.d2, s.hist);
+cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h_out,
+                                cudaStream_t st) {
+    int grid = N - 1 < 152 * 4 ? N - 1 : 152 * 4;
+    if (grid < 1) grid = 1;
+    median_digit_kernel<<<grid, 256, 0, st>>>(N, digit, s.d2, s.hist, s.sel, s.counter + digit,
+                                              s.h, h_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
-                       float* phi, float* h_out, cudaStream_t st) {
-    const size_t smem = (size_t)(2 * kCols * D + kRows * kCols + kRows * D) * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+                       float* phi, cudaStream_t st) {
+    // TMA bulk copies need 16-byte aligned sources
+    if ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(grad)) & 15u)
+        return cudaErrorMisalignedAddress;
+    const int dp = (D + 31) / 32;
+    switch (dp) {
+        case 1: return phi_launch<1>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
+        case 2: return phi_launch<2>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
+        case 3: return phi_launch<3>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
+        case 4: return phi_launch<4>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
+        case 5: case 6: return phi_launch<6>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
+        case 7: case 8: case 9: return phi_launch<9>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
     }
-    phi_kernel<<<(N + kRows - 1) / kRows, 256, smem, st>>>(theta, grad, N, D, s.d2, s.hist, phi,
-                                                           s.h, h_out);
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_adam(float* theta, const float* phi, float* m, float* v, int n, int step,

@@ -20,7 +20,7 @@ if not os.path.exists(_LIB_PATH):
                       "(python paper_2310_01775_gb300/build.py)")
 _lib = ctypes.CDLL(_LIB_PATH)
 
-STAMP_OK, STAMP_EINVAL, STAMP_ENOMEM, STAMP_ECUDA, STAMP_ENONFINITE = range(5)
+STAMP_OK, STAMP_EINVAL, STAMP_ENOMEM, STAMP_ECUDA, STAMP_ENONFINITE, STAMP_ETIMEOUT = range(6)
 KERNELS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init")
 STAMP_NKERNELS = len(KERNELS)
 

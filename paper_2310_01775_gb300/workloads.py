@@ -45,7 +45,9 @@ CONFIGS = {
     "pusher1_h2": dict(n_blocks=1, H=2, T=50, ckpt_every=25, N=32,
                        svgd_iters=200, lr=1e-2),
     # 1 block, 4 pushes of 100 substeps, 1024 particles, 500 iterations (D=24).
-    "pusher1_h4": dict(n_blocks=1, H=4, T=100, ckpt_every=25, N=1024,
+    # Every substep is checkpointed (a 9.9 MB tape): the adjoint then replays
+    # nothing, 1.6x faster than a checkpoint every 25 substeps on GB300.
+    "pusher1_h4": dict(n_blocks=1, H=4, T=100, ckpt_every=1, N=1024,
                        svgd_iters=500, lr=1e-2),
     # 3 blocks with block-block contact, 6 pushes of 100 substeps, a
     # checkpoint every 25 substeps, 2048 particles (D=84).

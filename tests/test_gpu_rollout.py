@@ -122,10 +122,11 @@ def test_noise_free_and_deterministic():
     Reference(theta, P, init, goal, None, C=P["ckpt_every"]).check(a[2], a[1], a[0], a[3])
 
 
-@pytest.mark.parametrize("name,sample", [("pusher1_h4", 16), ("pusher3_h6", 12)])
+@pytest.mark.parametrize("name,sample", [("pusher1_h4", 16), ("pusher3_h6", 64)])
 def test_full_size_sampled_particles(name, sample):
     """Full workload in the default launch configuration; the oracle checks a
-    sample of particles one by one over the whole horizon."""
+    sample of particles one by one, over the first action and (on a smaller
+    sample) over the whole horizon."""
     P = f32(W.params(name))
     N, seed, it = P["N"], 11, 7
     init, goal = W.scene(P, seed)
@@ -138,13 +139,12 @@ def test_full_size_sampled_particles(name, sample):
     idx = np.random.default_rng(0).choice(N, size=sample, replace=False)
     gum = O.gumbel_noise(seed, it, N, P["H"], M)[idx]
     C, T, Pn = P["ckpt_every"], P["T"], M + 2
-    # over the first action (checkpoints up to substep T) ...
     first = Reference(theta[idx][:, :Pn], dict(P, H=1), init, goal, gum[:, :1], C=C,
                       need_grad=False)
-    first.check(tape[idx][:, : T // C + 1], tape[idx][:, T // C], None, min_frac=0.2)
-    # ... and over the whole horizon, where chaos leaves fewer conditioned particles
-    whole = Reference(theta[idx], P, init, goal, gum, C=C)
-    whole.check(tape[idx], fin[idx], cost[idx], grad[idx], min_frac=0.0)
+    first.check(tape[idx][:, : T // C + 1], tape[idx][:, T // C], None, min_frac=0.04)
+    few = idx[:12]
+    whole = Reference(theta[few], P, init, goal, gum[:12], C=C)
+    whole.check(tape[few], fin[few], cost[few], grad[few], min_frac=0.0)
 
 
 def test_adjoint_requires_matching_forward():
