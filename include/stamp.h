@@ -185,6 +185,34 @@ stamp_status stamp_get_kernel_times(stamp_problem* prob, double* ms_out, long lo
 /* Lanes per particle used by the rollout kernels (1,2,4,8,16,32; 0 = automatic). */
 stamp_status stamp_set_lanes(stamp_problem* prob, int fwd_lanes, int adj_lanes);
 
+/* Stein step without any device allocation.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc -- code whose device memory
+ * belongs to someone else's allocator or pool (which must not be bypassed),
+ * code that runs where allocating is forbidden, or a device whose memory is
+ * already fully reserved -- and so cannot create a stamp_problem.
+ * It computes exactly what stamp_svgd_step computes (same kernels, same
+ * arguments and layouts) for N <= STAMP_NOALLOC_MAX_N particles of dimension
+ * D <= STAMP_NOALLOC_MAX_D; larger sizes are rejected with STAMP_EINVAL.  Its
+ * scratch memory (pairwise distances, Stein direction, histograms, counters,
+ * bandwidth; about 5.4 MB) is one fixed device array that every GPU loading
+ * the library holds until the process exits.
+ *   theta, grad_logp: device N x D, 16-byte aligned; adam_m, adam_v: device
+ *   N x D; step >= 1; lr; sgd_phase; h_out, phi_out: device or NULL (as in
+ *   stamp_svgd_step); cuda_stream: the cudaStream_t to run on (NULL = legacy
+ *   default stream).
+ * The first call on a device sets up that device's scratch address (a symbol
+ * lookup and one 4-byte copy), so make it before any stream capture.  The
+ * call waits for its stream and returns STAMP_ENONFINITE if a non-finite
+ * value appeared.  Every call shares the one array and it keeps the last
+ * call's contents (the call clears what must start at zero): calls that
+ * overlap on the GPU (other streams, other host threads) race. */
+#define STAMP_NOALLOC_MAX_N 1024
+#define STAMP_NOALLOC_MAX_D 288
+stamp_status stamp_svgd_step_noalloc(float* theta, const float* grad_logp, int N, int D,
+                                     float* adam_m, float* adam_v, int step, float lr,
+                                     int sgd_phase, float* h_out, float* phi_out,
+                                     void* cuda_stream);
+
 /* Static text of a status code, and the last error message of this thread. */
 const char* stamp_status_str(stamp_status s);
 const char* stamp_last_error(void);

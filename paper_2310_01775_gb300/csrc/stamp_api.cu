@@ -199,6 +199,8 @@ bool finite_nonneg(float x) { return std::isfinite(x) && x >= 0.f; }
 
 namespace stamp {
 
+void set_last_error(const char* msg) { g_err = msg; }
+
 bool lanes_supported(int nb, int lanes) {
     switch (nb) {
         case 1: return lanes == 1 || lanes == 2 || lanes == 4;

@@ -91,4 +91,7 @@ cudaError_t launch_init_theta(float* theta, int N, int D, uint64_t seed, cudaStr
 cudaError_t launch_topk(const float* theta, const float* cost, int N, const SimConst& sc, int k,
                         int* topk_out, cudaStream_t st);
 
+// Text returned by stamp_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 }  // namespace stamp

@@ -57,6 +57,7 @@ _sigs = {
     "stamp_get_kernel_times": [_vp, _vp, _vp],
     "stamp_set_lanes": [_vp, _i, _i],
     "stamp_dropped_gradients": [_vp, _vp],
+    "stamp_svgd_step_noalloc": [_vp, _vp, _i, _i, _vp, _vp, _i, _f, _i, _vp, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -163,6 +164,16 @@ def stamp_dropped_gradients(prob) -> int:
     n = ctypes.c_longlong()
     _check(_lib.stamp_dropped_gradients(prob, ctypes.byref(n)))
     return n.value
+
+
+def stamp_svgd_step_noalloc(theta, grad_logp, N, D, adam_m, adam_v, step, lr, sgd_phase=0,
+                            h_out=None, phi_out=None, cuda_stream=None):
+    """stamp_svgd_step for callers that cannot allocate device memory (its
+    scratch is a fixed array inside the library; N <= 1024, D <= 288)."""
+    _check(_lib.stamp_svgd_step_noalloc(_f32(theta, "theta"), _f32(grad_logp, "grad_logp"), N, D,
+                                        _f32(adam_m, "adam_m"), _f32(adam_v, "adam_v"), step, lr,
+                                        int(sgd_phase), _f32(h_out, "h_out"),
+                                        _f32(phi_out, "phi_out"), cuda_stream))
 
 
 def library_path() -> str:
