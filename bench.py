@@ -16,6 +16,7 @@ by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -35,6 +36,10 @@ UNIT = "particle-substeps/s"
 # oracle's own operations (oracle/flops.py): forward, reverse sweep.
 FLOPS_PER_UNIT = {1: (447.2, 863.2), 2: None, 3: (6293.5, 12860.9)}
 SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes, 1 FMA = 2 FLOP
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture (profiles/rollout_pusher1_h4.md), valid while the kernel source is
+# unchanged (sha256 prefix of csrc/rollout.cuh at capture time).
+TRAFFIC = {("pusher1_h4", "rollout_adj"): ("34b4f045baa4c0c3", 9.997824e6)}
 KERNEL_IDS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init")
 
 
@@ -247,8 +252,14 @@ def main():
         # the hard evaluation is also a forward launch: weight by the relaxed ones
         flops = (fpu[0] if dom == "rollout_fwd" else fpu[1]) * N * H * T
         ach = flops / (per_launch_ms / 1e3) / 1e12
+        traffic = None
+        src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2310_01775_gb300", "csrc",
+                                                    "rollout.cuh"), "rb").read()).hexdigest()[:16]
+        rec = TRAFFIC.get((args.workload, dom))
+        if rec and rec[0] == src_hash:
+            traffic = rec[1]
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": ach / peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / peak_tflops, "traffic": traffic,
                 "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz ({src})",
                 "ms_per_launch": per_launch_ms}
     cpu = None
