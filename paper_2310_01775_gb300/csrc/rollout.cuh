@@ -229,19 +229,15 @@ __device__ __forceinline__ void disk_box(const SimConst& sc, float px, float py,
     const float lx = cph * dx + sph * dy, ly = -sph * dx + cph * dy;
     const float qx = fabsf(lx) - sc.hs, qy = fabsf(ly) - sc.hs;
     const float sx = lx >= 0.f ? 1.f : -1.f, sy = ly >= 0.f ? 1.f : -1.f;
-    float sd, nlx, nly;
-    if (qx > 0.f || qy > 0.f) {
-        const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f);
-        const float l2 = mx * mx + my * my;
-        const float il = rsqrtf(l2);
-        sd = l2 * il;
-        nlx = sx * mx * il;
-        nly = sy * my * il;
-    } else if (qx >= qy) {
-        sd = qx; nlx = sx; nly = 0.f;
-    } else {
-        sd = qy; nlx = 0.f; nly = sy;
-    }
+    // outside: normalised clamped offset; inside: the axis of the larger q
+    // (selects, not branches: both are cheap and the chain stays straight)
+    const bool outside = qx > 0.f || qy > 0.f;
+    const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f);
+    const float il = rsqrtf(fmaxf(mx * mx + my * my, 1e-30f));
+    const bool xa = qx >= qy;
+    const float sd = outside ? (mx * mx + my * my) * il : fmaxf(qx, qy);
+    const float nlx = outside ? sx * mx * il : (xa ? sx : 0.f);
+    const float nly = outside ? sy * my * il : (xa ? 0.f : sy);
     const float delta = sc.r - sd;
     if (!(delta > 0.f)) return;
     const float nx = cph * nlx - sph * nly, ny = sph * nlx + cph * nly;
@@ -474,19 +470,11 @@ __device__ __forceinline__ DiskGrad disk_box_vjp(const SimConst& sc, float px, f
     const bool outside = qx > 0.f || qy > 0.f;
     const bool xa = qx >= qy;
     const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f);
-    float sd, nlx, nly, ln = 1.f, il = 1.f;
-    if (outside) {
-        const float l2 = mx * mx + my * my;
-        il = rsqrtf(l2);
-        ln = l2 * il;
-        sd = ln;
-        nlx = sx * mx * il;
-        nly = sy * my * il;
-    } else if (xa) {
-        sd = qx; nlx = sx; nly = 0.f;
-    } else {
-        sd = qy; nlx = 0.f; nly = sy;
-    }
+    const float il = rsqrtf(fmaxf(mx * mx + my * my, 1e-30f));
+    const float ln = (mx * mx + my * my) * il;
+    const float sd = outside ? ln : fmaxf(qx, qy);
+    const float nlx = outside ? sx * mx * il : (xa ? sx : 0.f);
+    const float nly = outside ? sy * my * il : (xa ? 0.f : sy);
     const float delta = sc.r - sd;
     if (!(delta > 0.f)) return g;
     const float nx = cph * nlx - sph * nly, ny = sph * nlx + cph * nly;
@@ -545,18 +533,11 @@ __device__ __forceinline__ DiskGrad disk_box_vjp(const SimConst& sc, float px, f
     float asph = -anx * nly + any * nlx;
     // delta = r - sd
     const float asd = -adelta;
-    float aqx, aqy;
-    if (outside) {
-        float amx = sx * anlx * il, amy = sy * anly * il;
-        const float aln = asd - (anlx * nlx + anly * nly) * il;
-        amx += aln * mx * il;
-        amy += aln * my * il;
-        aqx = qx > 0.f ? amx : 0.f;
-        aqy = qy > 0.f ? amy : 0.f;
-    } else {
-        aqx = xa ? asd : 0.f;
-        aqy = xa ? 0.f : asd;
-    }
+    // outside: through the normalised clamped offset; inside: the chosen axis
+    const float aln = asd - (anlx * nlx + anly * nly) * il;
+    const float amx = (sx * anlx + aln * mx) * il, amy = (sy * anly + aln * my) * il;
+    const float aqx = outside ? (qx > 0.f ? amx : 0.f) : (xa ? asd : 0.f);
+    const float aqy = outside ? (qy > 0.f ? amy : 0.f) : (xa ? 0.f : asd);
     const float alx = aqx * sx, aly = aqy * sy;
     const float adx = cph * alx - sph * aly, ady = sph * alx + cph * aly;
     acph += alx * dx + aly * dy;
@@ -662,10 +643,9 @@ __device__ __forceinline__ CornerGrad corner_vjp(const SimConst& sc, float xo, f
 // adjoints of the pusher start points, displacements and weights.
 template <int NB, int L>
 __device__ __forceinline__ void substep_vjp(const SimConst& sc, const Blocks<NB>& s,
+                                            const float (&cs)[NB], const float (&sn)[NB],
                                             const Slots<NB, L>& sl, SlotAcc<NB, L>& acc,
                                             const Corners<NB, L>& cn, float j1, Blocks<NB>& a) {
-    float cs[NB], sn[NB];
-    trig(s, cs, sn);
     float aFx[NB], aFy[NB], aT[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -788,10 +768,14 @@ __global__ void __launch_bounds__(128) rollout_adj_kernel(const SimConst sc, con
         load_state(tape_i + (size_t)(k * segs + segs - 1) * ck2, nxt);
         for (int sgi = segs - 1; sgi >= 0; --sgi) {
             s = nxt;
-            // prefetch the previous checkpoint; its latency hides behind this segment
+            // prefetch the previous checkpoint; its latency hides behind this
+            // segment (nothing here touches it before the next iteration: warps
+            // issue in order, so an early use would stall on the load)
             if (sgi > 0) load_state(tape_i + (size_t)(k * segs + sgi - 1) * ck2, nxt);
             if (sc.C == 1) {   // every state is on the tape: nothing to recompute
-                substep_vjp<NB, L>(sc, s, sl, acc, cn, (float)(sgi + 1), adj);
+                float cs[NB], sn[NB];
+                trig(s, cs, sn);
+                substep_vjp<NB, L>(sc, s, cs, sn, sl, acc, cn, (float)(sgi + 1), adj);
                 continue;
             }
             // recompute the segment forward, keeping the state before each substep
@@ -809,7 +793,9 @@ __global__ void __launch_bounds__(128) rollout_adj_kernel(const SimConst sc, con
             __syncwarp();
             for (int jj = sc.C - 1; jj >= 0; --jj) {
                 load_state(seg + jj * (S / 2), s);
-                substep_vjp<NB, L>(sc, s, sl, acc, cn, (float)(sgi * sc.C + jj + 1), adj);
+                float cs[NB], sn[NB];
+                trig(s, cs, sn);
+                substep_vjp<NB, L>(sc, s, cs, sn, sl, acc, cn, (float)(sgi * sc.C + jj + 1), adj);
             }
             __syncwarp();
         }
