@@ -159,10 +159,10 @@ stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
 stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, float* m, float* v,
                   int step, float lr, int sgd_phase, float* h_out, float* phi_out) {
     const int D = p->sc.D;
-    const float* dir = grad;
+    const float* part = grad;   // SGD phase: phi = grad log rho, one share
+    int shares = 1;
     if (!sgd_phase) {
         stamp::SvgdScratch s{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
-        float* phi = phi_out ? phi_out : p->phi;
         STAMP_CUDA(cudaMemsetAsync(p->hist, 0, (2048 + 2048 + 1024) * sizeof(unsigned), p->stream));
         STAMP_TRY(timed(p, STAMP_K_PAIRWISE,
                         [&] { return stamp::launch_pairwise(theta, N, D, s, p->stream); }));
@@ -176,19 +176,17 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
                                        p->stream));
         }
         STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
-            return stamp::launch_phi(theta, grad, N, D, s, phi, p->stream);
+            return stamp::launch_phi(theta, grad, N, D, s, p->phi, stamp::kMaxShares, &shares,
+                                     p->stream);
         }));
-        dir = phi;
-    } else {
-        if (phi_out)
-            STAMP_CUDA(cudaMemcpyAsync(phi_out, grad, (size_t)N * D * sizeof(float),
-                                       cudaMemcpyDeviceToDevice, p->stream));
-        if (h_out)
-            STAMP_CUDA(cudaMemcpyAsync(h_out, p->one, sizeof(float), cudaMemcpyDeviceToDevice,
-                                       p->stream));
+        part = p->phi;
+    } else if (h_out) {
+        STAMP_CUDA(cudaMemcpyAsync(h_out, p->one, sizeof(float), cudaMemcpyDeviceToDevice,
+                                   p->stream));
     }
     return timed(p, STAMP_K_ADAM, [&] {
-        return stamp::launch_adam(theta, dir, m, v, N * D, step, lr, p->flag, p->stream);
+        return stamp::launch_adam(theta, part, shares, phi_out, m, v, N * D, step, lr, p->flag,
+                                  p->stream);
     });
 }
 
@@ -322,7 +320,7 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         {(void**)&p->theta, n * D * sizeof(float)},
         {(void**)&p->m, n * D * sizeof(float)},
         {(void**)&p->v, n * D * sizeof(float)},
-        {(void**)&p->phi, n * D * sizeof(float)},
+        {(void**)&p->phi, (size_t)stamp::kMaxShares * n * D * sizeof(float)},
         {(void**)&p->d2, n * n * sizeof(float)},
         {(void**)&p->h, sizeof(float)},
         {(void**)&p->one, sizeof(float)},

@@ -13,6 +13,7 @@ namespace stamp {
 constexpr int kMaxBlocks = 4;     // n_blocks <= 4  ->  M = 4*n_blocks <= 16 choices
 constexpr int kMaxH = 16;         // plan codes pack 4 bits per action into 64 bits
 constexpr int kMaxTopkN = 8192;   // single-CTA bitonic sort of (cost, index)
+constexpr int kMaxShares = 8;     // partial Stein directions summed by the Adam kernel
 
 // Problem constants in the form the kernels use (derived once on the host).
 struct SimConst {
@@ -83,10 +84,14 @@ struct SvgdScratch {
 cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch& s, cudaStream_t st);
 cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h_out,
                                 cudaStream_t st);
+// Writes `*shares` partial Stein directions (N x D each, consecutive) to part;
+// at most max_shares.
 cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
-                       float* phi, cudaStream_t st);
-cudaError_t launch_adam(float* theta, const float* phi, float* m, float* v, int n_elems, int step,
-                        float lr, int* flag, cudaStream_t st);
+                       float* part, int max_shares, int* shares, cudaStream_t st);
+// Adam on -phi, phi = sum of the `shares` partials (stride n_elems); writes
+// phi to phi_out when given.
+cudaError_t launch_adam(float* theta, const float* part, int shares, float* phi_out, float* m,
+                        float* v, int n_elems, int step, float lr, int* flag, cudaStream_t st);
 cudaError_t launch_init_theta(float* theta, int N, int D, uint64_t seed, cudaStream_t st);
 cudaError_t launch_topk(const float* theta, const float* cost, int N, const SimConst& sc, int k,
                         int* topk_out, cudaStream_t st);

@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
                                                       const float* __restrict__ grad, int N, int D,
                                                       const float* __restrict__ d2,
                                                       const float* __restrict__ h_dev,
-                                                      float* __restrict__ phi, int* err) {
+                                                      float* __restrict__ part, int j_chunk,
+                                                      int* err) {
     extern __shared__ __align__(128) float sm[];
     const int sf = phi_stage_floats(D, DP);
     // stage s: theta tile at sm + 2*s*sf, grad tile right after it
@@ -258,7 +259,9 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
     uint64_t* bar = reinterpret_cast<uint64_t*>(Ks + kW * kTJ);       // 2 stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ib = (blockIdx.x * kW + warp) * kR;
-    const int ntiles = (N + kTJ - 1) / kTJ;
+    // this CTA's share of the sum over j: rows [jb, je) of theta and grad
+    const int jb = blockIdx.y * j_chunk, je = min(N, jb + j_chunk);
+    const int ntiles = (je - jb + kTJ - 1) / kTJ;
     const float inv_h = 1.f / __ldcg(h_dev);
 
     if (tid == 0) {
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
     // thread 0 streams tile t into stage t&1: the 16-byte-aligned bulk of the
     // contiguous rows by TMA, a ragged tail (< 16 bytes) by plain copies
     auto issue = [&](int t) {
-        const int s = t & 1, j0 = t * kTJ, n = min(kTJ, N - j0) * D;
+        const int s = t & 1, j0 = jb + t * kTJ, n = min(kTJ, je - j0) * D;
         const unsigned bulk = (unsigned)(n * 4) & ~15u;
         mbar_expect_tx(&bar[s], 2 * bulk);
         float* Ts = sm + 2 * s * sf;
@@ -297,11 +300,11 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
             ti[r][q] = (ib + r < N && d < D) ? theta[(size_t)(ib + r) * D + d] : 0.f;
             ag[r][q] = ar[r][q] = 0.f;
         }
-        dv[r] = (ib + r < N && lane < N) ? d2[(size_t)(ib + r) * N + lane] : 0.f;
+        dv[r] = (ib + r < N && jb + lane < je) ? d2[(size_t)(ib + r) * N + jb + lane] : 0.f;
     }
     unsigned phases = 0u;                       // bit s: parity of stage s
     for (int t = 0; t < ntiles; ++t) {
-        const int s = t & 1, j0 = t * kTJ, nj = min(kTJ, N - j0);
+        const int s = t & 1, j0 = jb + t * kTJ, nj = min(kTJ, je - j0);
         {
             float kv[kR];
 #pragma unroll
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
         if (t + 1 < ntiles) {   // next tile's distances, consumed one iteration later
             const int jn = j0 + kTJ + lane;
 #pragma unroll
-            for (int r = 0; r < kR; ++r) dv[r] = (ib + r < N && jn < N) ? d2[(size_t)(ib + r) * N + jn] : 0.f;
+            for (int r = 0; r < kR; ++r) dv[r] = (ib + r < N && jn < je) ? d2[(size_t)(ib + r) * N + jn] : 0.f;
         }
         const unsigned par = (phases >> s) & 1u;
         unsigned spins = 0;
@@ -354,24 +357,32 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
             issue(t + 2);
         }
     }
+    // partial phi of this j-share; the Adam kernel sums the shares in order
     const float inv_n = 1.f / (float)N, two_h = 2.f * inv_h;
+    float* out = part + (size_t)blockIdx.y * N * D;
 #pragma unroll
     for (int r = 0; r < kR; ++r)
 #pragma unroll
         for (int q = 0; q < DP; ++q) {
             const int d = lane + 32 * q;
             if (ib + r < N && d < D)
-                phi[(size_t)(ib + r) * D + d] = (ag[r][q] + two_h * ar[r][q]) * inv_n;
+                out[(size_t)(ib + r) * D + d] = (ag[r][q] + two_h * ar[r][q]) * inv_n;
         }
 }
 
-// Adam (Kingma & Ba 2015) with gradient -phi; flags non-finite inputs/results.
-__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ phi,
-                            float* __restrict__ m, float* __restrict__ v, int n, float lr,
-                            float bc1, float bc2, int* flag) {
+// Adam (Kingma & Ba 2015) with gradient -phi, phi the in-order sum of the
+// `shares` partial directions (stride n); optionally stores phi.  Flags
+// non-finite inputs/results.
+__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ part, int shares,
+                            float* __restrict__ phi_out, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float bc1, float bc2,
+                            int* flag) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const float g = -phi[t];
+    float phi = part[t];
+    for (int q = 1; q < shares; ++q) phi += part[(size_t)q * n + t];
+    if (phi_out) phi_out[t] = phi;
+    const float g = -phi;
     const float mt = 0.9f * m[t] + 0.1f * g;
     const float vt = 0.999f * v[t] + 0.001f * g * g;
     const float th = theta[t] - lr * (mt / bc1) / (sqrtf(vt / bc2) + 1e-8f);
@@ -443,7 +454,8 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ th
 
 template <int DP>
 cudaError_t phi_launch(const float* theta, const float* grad, int N, int D, const float* d2,
-                       const float* h_dev, float* phi, int* err, cudaStream_t st) {
+                       const float* h_dev, float* part, int shares, int j_chunk, int* err,
+                       cudaStream_t st) {
     const size_t smem = (size_t)4 * phi_stage_floats(D, DP) * sizeof(float) +
                         (size_t)kW * kTJ * sizeof(float4) + 2 * sizeof(uint64_t);
     if (smem > 48 * 1024) {
@@ -452,8 +464,8 @@ cudaError_t phi_launch(const float* theta, const float* grad, int N, int D, cons
         if (e != cudaSuccess) return e;
     }
     const int rows = kW * kR;
-    phi_kernel<DP><<<(N + rows - 1) / rows, kW * 32, smem, st>>>(theta, grad, N, D, d2, h_dev, phi,
-                                                                 err);
+    phi_kernel<DP><<<dim3((N + rows - 1) / rows, shares), kW * 32, smem, st>>>(
+        theta, grad, N, D, d2, h_dev, part, j_chunk, err);
     return cudaGetLastError();
 }
 
@@ -475,7 +487,7 @@ cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch&
 
 cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h_out,
                                 cudaStream_t st) {
-    int grid = N - 1 < 152 * 4 ? N - 1 : 152 * 4;
+    int grid = N - 1 < 152 * 2 ? N - 1 : 152 * 2;
     if (grid < 1) grid = 1;
     median_digit_kernel<<<grid, 256, 0, st>>>(N, digit, s.d2, s.hist, s.sel, s.counter + digit,
                                               s.h, h_out);
@@ -483,27 +495,37 @@ cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h
 }
 
 cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
-                       float* phi, cudaStream_t st) {
+                       float* part, int max_shares, int* shares, cudaStream_t st) {
     // TMA bulk copies need 16-byte aligned sources
     if ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(grad)) & 15u)
         return cudaErrorMisalignedAddress;
+    // split the sum over j so that about four CTAs per SM are in flight; the
+    // shares start on kTJ-row boundaries (16-byte aligned TMA sources)
+    const int row_blocks = (N + kW * kR - 1) / (kW * kR);
+    int want = (4 * 152 + row_blocks - 1) / row_blocks;
+    want = want < 1 ? 1 : (want > max_shares ? max_shares : want);
+    const int j_chunk = ((N + want - 1) / want + kTJ - 1) / kTJ * kTJ;
+    *shares = (N + j_chunk - 1) / j_chunk;
     const int dp = (D + 31) / 32;
     switch (dp) {
-        case 1: return phi_launch<1>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
-        case 2: return phi_launch<2>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
-        case 3: return phi_launch<3>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
-        case 4: return phi_launch<4>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
-        case 5: case 6: return phi_launch<6>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
-        case 7: case 8: case 9: return phi_launch<9>(theta, grad, N, D, s.d2, s.h, phi, s.err, st);
+        case 1: return phi_launch<1>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+        case 2: return phi_launch<2>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+        case 3: return phi_launch<3>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+        case 4: return phi_launch<4>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+        case 5: case 6:
+            return phi_launch<6>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+        case 7: case 8: case 9:
+            return phi_launch<9>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_adam(float* theta, const float* phi, float* m, float* v, int n, int step,
-                        float lr, int* flag, cudaStream_t st) {
+cudaError_t launch_adam(float* theta, const float* part, int shares, float* phi_out, float* m,
+                        float* v, int n, int step, float lr, int* flag, cudaStream_t st) {
     const float bc1 = 1.f - powf(0.9f, (float)step);
     const float bc2 = 1.f - powf(0.999f, (float)step);
-    adam_kernel<<<(n + 255) / 256, 256, 0, st>>>(theta, phi, m, v, n, lr, bc1, bc2, flag);
+    adam_kernel<<<(n + 255) / 256, 256, 0, st>>>(theta, part, shares, phi_out, m, v, n, lr, bc1,
+                                                 bc2, flag);
     return cudaGetLastError();
 }
 

@@ -123,27 +123,24 @@ extern "C" stamp_status stamp_svgd_step_noalloc(float* theta, const float* grad_
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffCounter, 0, 256, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffFlag, 0, sizeof(int), s);
     if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "clearing the scratch failed", e);
-    const float* dir = grad_logp;
+    const float* part = grad_logp;   // SGD phase: phi = grad log rho
+    int shares = 1;
     const float* h_src = reinterpret_cast<const float*>(base + kOffOne);
     if (!sgd_phase) {
-        float* phi = phi_out ? phi_out : reinterpret_cast<float*>(base + kOffPhi);
+        float* phi = reinterpret_cast<float*>(base + kOffPhi);   // room for one share
         e = stamp::launch_pairwise(theta, N, D, sc, s);
         for (int dg = 1; dg <= 2 && e == cudaSuccess && N >= 2; ++dg)
             e = stamp::launch_median_digit(N, dg, sc, nullptr, s);
-        if (e == cudaSuccess) e = stamp::launch_phi(theta, grad_logp, N, D, sc, phi, s);
+        if (e == cudaSuccess) e = stamp::launch_phi(theta, grad_logp, N, D, sc, phi, 1, &shares, s);
         if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "Stein direction launch failed", e);
-        dir = phi;
+        part = phi;
         h_src = sc.h;
-    } else if (phi_out) {
-        e = cudaMemcpyAsync(phi_out, grad_logp, (size_t)N * D * sizeof(float),
-                            cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "copy of phi failed", e);
     }
     if (h_out) {
         e = cudaMemcpyAsync(h_out, h_src, sizeof(float), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "copy of h failed", e);
     }
-    e = stamp::launch_adam(theta, dir, adam_m, adam_v, N * D, step, lr, sc.err, s);
+    e = stamp::launch_adam(theta, part, shares, phi_out, adam_m, adam_v, N * D, step, lr, sc.err, s);
     if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "Adam launch failed", e);
     int flag = 0;
     e = cudaMemcpyAsync(&flag, sc.err, sizeof flag, cudaMemcpyDeviceToHost, s);

@@ -16,6 +16,12 @@ from paper_2310_01775_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
+def _close(x, y, rel=1e-5):
+    """Max-norm relative agreement (the bar of the Stein-step parity tests):
+    the two paths may sum the Stein direction over j in different groupings."""
+    return float((x - y).abs().max()) <= rel * max(float(y.abs().max()), 1e-12)
+
+
 def _inputs(N, D, seed):
     theta = W.random_theta(N, D, seed)
     g = W.random_normal((N, D), seed + 1)
@@ -43,9 +49,9 @@ def test_noalloc_step_matches_problem_step_twice(N, name, sgd):
         prob.sync()
         S.stamp_svgd_step_noalloc(b[0], b[1], N, D, b[2], b[3], step, 1e-2, sgd, hb, pb, stream)
         assert abs(float(ha) - float(hb)) <= 1e-5 * abs(float(ha))
-        assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-9)
-        for x, y in zip(a, b):
-            assert torch.allclose(x, y, rtol=1e-5, atol=1e-7)
+        assert _close(pb, pa)
+        for x, y in zip(b, a):
+            assert _close(x, y)
         a[1] = torch.roll(a[1], 1, 0).contiguous()   # next gradients
         b[1] = a[1].clone()
     prob.close()
