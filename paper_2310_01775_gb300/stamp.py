@@ -206,6 +206,7 @@ class Problem:
             pass
 
     def rollout_fwd(self, theta, N, seed, iter, hard, cost, final_state=None):
+        self._tape_owner = None          # the tape now belongs to this call
         stamp_rollout_fwd(self.handle, theta, N, seed, iter, hard, cost, final_state)
 
     def rollout_adjoint(self, theta, N, seed, iter, grad_logp):
@@ -221,6 +222,7 @@ class Problem:
 
     def solve(self, N, svgd_iters, sgd_iters, seed, lr, theta_init, theta_out, cost_out=None, k=0,
               topk_particle=None, stats_out=None):
+        self._tape_owner = None
         stamp_solve(self.handle, N, svgd_iters, sgd_iters, seed, lr, theta_init, theta_out,
                     cost_out, k, topk_particle, stats_out)
 
