@@ -213,6 +213,27 @@ stamp_status stamp_svgd_step_noalloc(float* theta, const float* grad_logp, int N
                                      int sgd_phase, float* h_out, float* phi_out,
                                      void* cuda_stream);
 
+/* ---- MLP dynamics surrogate (BF16 tensor cores) ---------------------------
+ * A 4-layer perceptron in_dim -> 256 -> 256 -> 256 -> out_dim with SiLU
+ * activations and a linear head, BF16 weights and activations, FP32
+ * accumulation (tcgen05 MMA into tensor memory).  It stands in for the
+ * simulator's per-push transition (the learned dynamics of the surrogate
+ * workload; the paper itself simulates every plan, Sec. III-B). */
+typedef struct stamp_mlp stamp_mlp;
+/* 1 <= in_dim <= 32, 1 <= out_dim <= 16; scratch for up to max_rows rows. */
+stamp_status stamp_mlp_create(int in_dim, int out_dim, int max_rows, void* cuda_stream,
+                              stamp_mlp** out);
+void stamp_mlp_destroy(stamp_mlp* mlp);
+/* Number of floats of the packed parameter vector: for each layer l, W_l as
+ * (out_l, in_l) row-major, then b_l (out_l). */
+size_t stamp_mlp_param_count(int in_dim, int out_dim);
+/* params: device, the packed FP32 parameters; converted to BF16 tiles. */
+stamp_status stamp_mlp_set_params(stamp_mlp* mlp, const float* params);
+/* y (device rows x out_dim FP32) = MLP(x (device rows x in_dim FP32)); asynchronous. */
+stamp_status stamp_mlp_forward(stamp_mlp* mlp, const float* x, int rows, float* y);
+/* Wait for the MLP's stream; STAMP_ETIMEOUT if a bounded device wait gave up. */
+stamp_status stamp_mlp_sync(stamp_mlp* mlp);
+
 /* Static text of a status code, and the last error message of this thread. */
 const char* stamp_status_str(stamp_status s);
 const char* stamp_last_error(void);

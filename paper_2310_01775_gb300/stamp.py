@@ -58,10 +58,18 @@ _sigs = {
     "stamp_set_lanes": [_vp, _i, _i],
     "stamp_dropped_gradients": [_vp, _vp],
     "stamp_svgd_step_noalloc": [_vp, _vp, _i, _i, _vp, _vp, _i, _f, _i, _vp, _vp, _vp],
+    "stamp_mlp_create": [_i, _i, _i, _vp, ctypes.POINTER(_vp)],
+    "stamp_mlp_set_params": [_vp, _vp],
+    "stamp_mlp_forward": [_vp, _vp, _i, _vp],
+    "stamp_mlp_sync": [_vp],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int
+_lib.stamp_mlp_destroy.argtypes = [_vp]
+_lib.stamp_mlp_destroy.restype = None
+_lib.stamp_mlp_param_count.argtypes = [_i, _i]
+_lib.stamp_mlp_param_count.restype = ctypes.c_size_t
 _lib.stamp_problem_destroy.argtypes = [_vp]
 _lib.stamp_problem_destroy.restype = None
 _lib.stamp_status_str.argtypes = [ctypes.c_int]
@@ -240,3 +248,35 @@ class Problem:
 
     def dropped_gradients(self):
         return stamp_dropped_gradients(self.handle)
+
+
+class MLP:
+    """The BF16 tensor-core MLP (in_dim -> 256 -> 256 -> 256 -> out_dim, SiLU)."""
+
+    def __init__(self, in_dim: int, out_dim: int, max_rows: int, cuda_stream: int | None = None):
+        self.in_dim, self.out_dim = in_dim, out_dim
+        out = _vp()
+        _check(_lib.stamp_mlp_create(in_dim, out_dim, max_rows, cuda_stream, ctypes.byref(out)))
+        self.handle = out.value
+        self.n_params = int(_lib.stamp_mlp_param_count(in_dim, out_dim))
+
+    def close(self):
+        if self.handle:
+            _lib.stamp_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        """params: device float32 vector W1,b1,...,W4,b4 (W as (out, in))."""
+        _check(_lib.stamp_mlp_set_params(self.handle, _f32(params, "params")))
+
+    def forward(self, x, rows, y):
+        _check(_lib.stamp_mlp_forward(self.handle, _f32(x, "x"), rows, _f32(y, "y")))
+
+    def sync(self):
+        _check(_lib.stamp_mlp_sync(self.handle))

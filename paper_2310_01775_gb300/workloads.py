@@ -111,3 +111,14 @@ def random_normal(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     """Parity-test arrays (gradients, Adam moments): N(0, scale^2), float32."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x6A55]))
     return (scale * rng.standard_normal(size=shape)).astype(np.float32)
+
+
+def mlp_init(sizes, seed: int):
+    """Initial MLP parameters [(W (out, in), b (out,))] per layer: uniform in
+    [-1/sqrt(in), 1/sqrt(in)], float64 (cast as needed)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x4D4C50]))
+    out = []
+    for i, o in zip(sizes[:-1], sizes[1:]):
+        k = 1.0 / math.sqrt(i)
+        out.append((rng.uniform(-k, k, size=(o, i)), rng.uniform(-k, k, size=o)))
+    return out
