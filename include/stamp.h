@@ -220,9 +220,11 @@ stamp_status stamp_svgd_step_noalloc(float* theta, const float* grad_logp, int N
  * simulator's per-push transition (the learned dynamics of the surrogate
  * workload; the paper itself simulates every plan, Sec. III-B). */
 typedef struct stamp_mlp stamp_mlp;
-/* 1 <= in_dim <= 32, 1 <= out_dim <= 16; scratch for up to max_rows rows. */
-stamp_status stamp_mlp_create(int in_dim, int out_dim, int max_rows, void* cuda_stream,
-                              stamp_mlp** out);
+/* 1 <= in_dim <= 32, 1 <= out_dim <= 16; scratch for up to max_rows rows per
+ * forward, and saved activations (about 5.8 KB per row) for train_rows rows
+ * for the backward pass (0: inference only). */
+stamp_status stamp_mlp_create(int in_dim, int out_dim, int max_rows, int train_rows,
+                              void* cuda_stream, stamp_mlp** out);
 void stamp_mlp_destroy(stamp_mlp* mlp);
 /* Number of floats of the packed parameter vector: for each layer l, W_l as
  * (out_l, in_l) row-major, then b_l (out_l). */
@@ -231,6 +233,24 @@ size_t stamp_mlp_param_count(int in_dim, int out_dim);
 stamp_status stamp_mlp_set_params(stamp_mlp* mlp, const float* params);
 /* y (device rows x out_dim FP32) = MLP(x (device rows x in_dim FP32)); asynchronous. */
 stamp_status stamp_mlp_forward(stamp_mlp* mlp, const float* x, int rows, float* y);
+/* The same, keeping the activations for stamp_mlp_backward in the saved
+ * tiles [tile_base, tile_base + ceil(rows/128)) (several batches, e.g. the
+ * pushes of a plan, can be kept side by side). */
+stamp_status stamp_mlp_forward_saved(stamp_mlp* mlp, const float* x, int rows, float* y,
+                                     int tile_base);
+/* Reverse sweep of the forward saved at tile_base: given dy = dL/dy (device
+ * rows x out_dim), writes dx = dL/dx (device rows x in_dim, or NULL) and
+ * dparams = dL/dparams (device, packed like the parameters, or NULL).  The
+ * input gradient runs on the tensor cores (BF16, FP32 accumulation); the
+ * weight gradients are FP32 reductions over the rows on the CUDA cores. */
+stamp_status stamp_mlp_backward(stamp_mlp* mlp, const float* dy, int rows, int tile_base,
+                                float* dx, float* dparams);
+/* Adam (lr, beta 0.9/0.999) on the mean squared error of MLP(x) against
+ * target (device rows x in_dim / rows x out_dim), minibatches of `batch`
+ * consecutive rows, `epochs` passes; params (device, packed) updated in place;
+ * loss_out: host, mean loss of each epoch (or NULL).  Waits for the stream. */
+stamp_status stamp_mlp_train(stamp_mlp* mlp, float* params, const float* x, const float* target,
+                             int rows, int epochs, int batch, float lr, float* loss_out);
 /* Wait for the MLP's stream; STAMP_ETIMEOUT if a bounded device wait gave up. */
 stamp_status stamp_mlp_sync(stamp_mlp* mlp);
 

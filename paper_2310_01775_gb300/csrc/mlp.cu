@@ -14,6 +14,7 @@
 // each layer's epilogue writes the next layer's A operand straight into it.
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "mlp.cuh"
 #include "stamp.h"
@@ -164,12 +165,14 @@ __host__ __device__ constexpr int layer_k(int l) { return l == 0 ? kIn : kHidden
 __host__ __device__ constexpr int layer_n(int l) { return l == 3 ? kOut : kHidden; }
 
 // Forward of all four layers for 128-row tiles; y: rows x kOut FP32.
-// Optionally stores every layer's input activation (BF16, tiled) for the
-// backward pass: saved + l * rows_pad * kHidden * 2 bytes (layer 0 input is x).
+// Optionally stores, for the backward pass, the input activations a_1..a_3 and
+// the pre-activations z_0..z_2 (BF16 tiles): slot (l, tile_base + tile) of
+// buffers holding tile_cap tiles per layer.
 __global__ void __launch_bounds__(kThreads, 1)
 mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
                const unsigned char* __restrict__ w_tiled, const float* __restrict__ bias,
                float* __restrict__ y, int rows, unsigned char* __restrict__ saved,
+               unsigned char* __restrict__ zsave, int tile_base, int tile_cap,
                int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     FwdSmem& sm = *reinterpret_cast<FwdSmem*>(smem_raw);
@@ -202,7 +205,7 @@ mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
             tma_phase ^= 1u;
             if (__syncthreads_or(spins >= kWaitLimit)) { failed = true; break; }
             if (saved && l > 0) {   // this layer's input activation, for the backward pass
-                unsigned char* dst = saved + ((size_t)l * n_tiles + tile) * kActBytes;
+                unsigned char* dst = saved + ((size_t)l * tile_cap + tile_base + tile) * kActBytes;
                 for (int b = tid * 16; b < (int)kActBytes; b += kThreads * 16)
                     *reinterpret_cast<uint4*>(dst + b) = *reinterpret_cast<const uint4*>(sm.act + b);
             }
@@ -232,13 +235,21 @@ mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
                     for (int q = 0; q < 4; ++q) {
                         uint4 pk;
                         unsigned* pw = reinterpret_cast<unsigned*>(&pk);
+                        uint4 pz;
+                        unsigned* pzw = reinterpret_cast<unsigned*>(&pz);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int c = c0 + q * 8 + 2 * e;
-                            pw[e] = pack_bf16(silu(v[q * 8 + 2 * e] + __ldg(bl + c)),
-                                              silu(v[q * 8 + 2 * e + 1] + __ldg(bl + c + 1)));
+                            const float z0 = v[q * 8 + 2 * e] + __ldg(bl + c);
+                            const float z1 = v[q * 8 + 2 * e + 1] + __ldg(bl + c + 1);
+                            pw[e] = pack_bf16(silu(z0), silu(z1));
+                            pzw[e] = pack_bf16(z0, z1);
                         }
-                        *reinterpret_cast<uint4*>(sm.act + tile_off(row, c0 + q * 8, kHidden)) = pk;
+                        const unsigned off = tile_off(row, c0 + q * 8, kHidden);
+                        *reinterpret_cast<uint4*>(sm.act + off) = pk;
+                        if (zsave)   // pre-activation of layer l, for the backward pass
+                            *reinterpret_cast<uint4*>(
+                                zsave + ((size_t)l * tile_cap + tile_base + tile) * kActBytes + off) = pz;
                     }
                 }
             } else {
@@ -290,16 +301,18 @@ __global__ void pack_input_kernel(const float* __restrict__ x, int rows, int in_
 // Master FP32 parameters (W_l as (n_l, k_l) real sizes, then b_l) -> packed BF16
 // K-major weight tiles (zero-padded to the kernel's sizes) and FP32 biases.
 __global__ void pack_weights_kernel(const float* __restrict__ params, int in_dim, int out_dim,
-                                    unsigned char* __restrict__ w_tiled, float* __restrict__ bias) {
+                                    unsigned char* __restrict__ w_tiled,
+                                    unsigned char* __restrict__ wt_tiled, float* __restrict__ bias) {
     const int l = blockIdx.y;
     const int K = layer_k(l), N = layer_n(l);
     const int kr = l == 0 ? in_dim : kHidden, nr = l == 3 ? out_dim : kHidden;
     const float* W = params + param_offset(l, in_dim, out_dim);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N * K; t += gridDim.x * blockDim.x) {
         const int n = t / K, k = t % K;
-        const float v = (n < nr && k < kr) ? W[n * kr + k] : 0.f;
-        *reinterpret_cast<__nv_bfloat16*>(w_tiled + layer_w_offset(l) + tile_off(n, k, K)) =
-            __float2bfloat16_rn(v);
+        const __nv_bfloat16 v = __float2bfloat16_rn((n < nr && k < kr) ? W[n * kr + k] : 0.f);
+        // forward operand: (N = out, K = in); backward operand W^T: (N = in, K = out)
+        *reinterpret_cast<__nv_bfloat16*>(w_tiled + layer_w_offset(l) + tile_off(n, k, K)) = v;
+        *reinterpret_cast<__nv_bfloat16*>(wt_tiled + layer_w_offset(l) + tile_off(k, n, N)) = v;
     }
     if (blockIdx.x == 0)
         for (int n = threadIdx.x; n < kHidden; n += blockDim.x)
@@ -312,33 +325,295 @@ __global__ void unpack_output_kernel(const float* __restrict__ ypad, int rows, i
     if (t < rows * out_dim) y[t] = ypad[(size_t)(t / out_dim) * kOut + t % out_dim];
 }
 
+__device__ __forceinline__ float silu_grad(float z) {
+    const float sg = 1.f / (1.f + __expf(-z));
+    return sg * (1.f + z * (1.f - sg));
+}
+__device__ __forceinline__ float bf_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(unsigned w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// Reverse sweep through the four layers for 128-row tiles:
+//   dz_3 = dy;  da_m = dz_m W_m (MMA, B = W_m^T tiles);  dz_{m-1} = da_m * SiLU'(z_{m-1});
+//   dx = da_0.
+// dz_m (BF16 tiles) go to dzsave slot (m, tile_base + tile) for the weight
+// gradients; zsave holds the forward's pre-activations.
+__global__ void __launch_bounds__(kThreads, 1)
+mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
+               const unsigned char* __restrict__ wt_tiled, const unsigned char* __restrict__ zsave,
+               unsigned char* __restrict__ dzsave, int tile_base, int tile_cap,
+               float* __restrict__ dx, int in_dim, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    FwdSmem& sm = *reinterpret_cast<FwdSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&sm.tma_bar, 1);
+        mbar_init(&sm.mma_bar, 1);
+        fence_async_shared();
+    }
+    if (warp == 0) tmem_alloc(&sm.tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = sm.tmem_slot;
+    const int row = warp * 32 + lane;
+    unsigned tma_phase = 0, mma_phase = 0;
+    bool failed = false;
+    for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        const int r = tile * kRows + row;
+        const size_t slot = (size_t)tile_base + tile;
+        {   // dz_3 = dy as a BF16 K-major tile of 16 columns
+            float d[kOut];
+#pragma unroll
+            for (int c = 0; c < kOut; ++c) d[c] = (r < rows && c < out_dim) ? dy[(size_t)r * out_dim + c] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint4 pk;
+                unsigned* pw = reinterpret_cast<unsigned*>(&pk);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) pw[e] = pack_bf16(d[q * 8 + 2 * e], d[q * 8 + 2 * e + 1]);
+                const unsigned off = tile_off(row, q * 8, kOut);
+                *reinterpret_cast<uint4*>(sm.act + off) = pk;
+                *reinterpret_cast<uint4*>(dzsave + ((size_t)3 * tile_cap + slot) * kActBytes + off) = pk;
+            }
+        }
+        fence_async_shared();
+        __syncthreads();
+        for (int m = 3; m >= 0 && !failed; --m) {
+            const int Kb = layer_n(m), Nb = layer_k(m);   // da_m = dz_m (., Kb) W_m (Kb, Nb)
+            if (tid == 0) {
+                const unsigned wbytes = (unsigned)(Nb * Kb * 2);
+                mbar_expect_tx(&sm.tma_bar, wbytes);
+                tma_load_1d(sm.w, wt_tiled + layer_w_offset(m), wbytes, &sm.tma_bar);
+            }
+            unsigned spins = 0;
+            while (!mbar_try_wait(&sm.tma_bar, tma_phase) && ++spins < kWaitLimit) {
+            }
+            tma_phase ^= 1u;
+            if (__syncthreads_or(spins >= kWaitLimit)) { failed = true; break; }
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t idesc = idesc_bf16(kRows, Nb);
+                for (int kk = 0; kk < Kb / 16; ++kk)
+                    mma_bf16(tmem, smem_desc(sm.act + kk * 256, 128, (Kb / 8) * 128),
+                             smem_desc(sm.w + kk * 256, 128, (Kb / 8) * 128), idesc, kk > 0);
+                mma_commit(&sm.mma_bar);
+            }
+            spins = 0;
+            while (!mbar_try_wait(&sm.mma_bar, mma_phase) && ++spins < kWaitLimit) {
+            }
+            mma_phase ^= 1u;
+            if (__syncthreads_or(spins >= kWaitLimit)) { failed = true; break; }
+            tc_fence_after();
+            const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+            if (m > 0) {
+                const unsigned char* zt = zsave + ((size_t)(m - 1) * tile_cap + slot) * kActBytes;
+                unsigned char* dzt = dzsave + ((size_t)(m - 1) * tile_cap + slot) * kActBytes;
+                for (int c0 = 0; c0 < kHidden; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(lane_base + c0, v);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const unsigned off = tile_off(row, c0 + q * 8, kHidden);
+                        const uint4 zq = *reinterpret_cast<const uint4*>(zt + off);
+                        const unsigned zw[4] = {zq.x, zq.y, zq.z, zq.w};
+                        uint4 pk;
+                        unsigned* pw = reinterpret_cast<unsigned*>(&pk);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            pw[e] = pack_bf16(v[q * 8 + 2 * e] * silu_grad(bf_lo(zw[e])),
+                                              v[q * 8 + 2 * e + 1] * silu_grad(bf_hi(zw[e])));
+                        *reinterpret_cast<uint4*>(sm.act + off) = pk;
+                        *reinterpret_cast<uint4*>(dzt + off) = pk;
+                    }
+                }
+            } else if (dx) {
+                float v[32];
+                tmem_ld32(lane_base, v);
+                if (r < rows)
+                    for (int c = 0; c < in_dim; ++c) dx[(size_t)r * in_dim + c] = v[c];
+            }
+            fence_async_shared();
+            tc_fence_before();
+            __syncthreads();
+        }
+    }
+    if (failed && tid == 0) {
+        atomicOr(err, 2);
+        for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.tma_bar, tma_phase ^ 1u); ++w) {
+        }
+        for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.mma_bar, mma_phase ^ 1u); ++w) {
+        }
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// Element (row r, column c) of consecutive K-column BF16 tiles of 128 rows,
+// `stride` bytes apart.
+__device__ __forceinline__ float tiled_at(const unsigned char* base, size_t stride, int r, int c,
+                                          int K) {
+    const unsigned short h = *reinterpret_cast<const unsigned short*>(
+        base + (size_t)(r >> 7) * stride + tile_off(r & 127, c, K));
+    return __uint_as_float((unsigned)h << 16);
+}
+
+// dW_l (out_r x in_r, FP32, added to) += sum over rows of dz_l[r][o] a_l[r][i]:
+// 64 x 64 output tiles, rows split over blockIdx.z, FP32 accumulation on
+// CUDA cores, one atomic add per output and block.
+__global__ void __launch_bounds__(256) mlp_dw_kernel(const unsigned char* __restrict__ a, int Ka,
+                                                     size_t a_stride,
+                                                     const unsigned char* __restrict__ dz, int Kd,
+                                                     int rows, int out_r, int in_r, int row_chunk,
+                                                     float* __restrict__ dW) {
+    __shared__ float ds[32][65], as[32][65];
+    const int o0 = blockIdx.y * 64, i0 = blockIdx.x * 64;
+    const int rb = blockIdx.z * row_chunk, re = min(rows, rb + row_chunk);
+    const int to = threadIdx.x / 16, ti = threadIdx.x % 16;
+    float acc[4][4] = {};
+    for (int r0 = rb; r0 < re; r0 += 32) {
+        for (int t = threadIdx.x; t < 32 * 64; t += 256) {
+            const int rr = t / 64, cc = t % 64, r = r0 + rr;
+            ds[rr][cc] = (r < re && o0 + cc < out_r) ? tiled_at(dz, kActBytes, r, o0 + cc, Kd) : 0.f;
+            as[rr][cc] = (r < re && i0 + cc < in_r) ? tiled_at(a, a_stride, r, i0 + cc, Ka) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            float dv[4], av[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) { dv[p] = ds[k][to * 4 + p]; av[p] = as[k][ti * 4 + p]; }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(dv[p], av[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int o = o0 + to * 4 + p, i = i0 + ti * 4 + q;
+            if (o < out_r && i < in_r) atomicAdd(&dW[(size_t)o * in_r + i], acc[p][q]);
+        }
+}
+
+// db_l[o] += sum over rows of dz_l[r][o].
+__global__ void mlp_db_kernel(const unsigned char* __restrict__ dz, int Kd, int rows, int out_r,
+                              int row_chunk, float* __restrict__ db) {
+    const int o = threadIdx.x;
+    if (o >= out_r) return;
+    const int rb = blockIdx.x * row_chunk, re = min(rows, rb + row_chunk);
+    float s = 0.f;
+    for (int r = rb; r < re; ++r) s += tiled_at(dz, kActBytes, r, o, Kd);
+    atomicAdd(&db[o], s);
+}
+
+// Mean squared error over rows x out_dim: dy = 2 (y - t) / n, loss += sum (y-t)^2 / n.
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, int n,
+                           float* __restrict__ dy, float* __restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float e2 = 0.f;
+    if (i < n) {
+        const float e = y[i] - t[i];
+        dy[i] = 2.f * e / (float)n;
+        e2 = e * e / (float)n;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    if ((threadIdx.x & 31) == 0 && e2 != 0.f) atomicAdd(loss, e2);
+}
+
+// Adam (Kingma & Ba 2015) minimising along g.
+__global__ void param_adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                                  float* __restrict__ m, float* __restrict__ v, int n, float lr,
+                                  float bc1, float bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mt = 0.9f * m[i] + 0.1f * g[i];
+    const float vt = 0.999f * v[i] + 0.001f * g[i] * g[i];
+    m[i] = mt;
+    v[i] = vt;
+    p[i] -= lr * (mt / bc1) / (sqrtf(vt / bc2) + 1e-8f);
+}
+
 }  // namespace
 
 size_t fwd_smem_bytes() { return sizeof(FwdSmem) + 1024; }
 
 cudaError_t pack_weights(const float* params, int in_dim, int out_dim, unsigned char* w_tiled,
-                         float* bias, cudaStream_t st) {
-    pack_weights_kernel<<<dim3(64, 4), 256, 0, st>>>(params, in_dim, out_dim, w_tiled, bias);
+                         unsigned char* wt_tiled, float* bias, cudaStream_t st) {
+    pack_weights_kernel<<<dim3(64, 4), 256, 0, st>>>(params, in_dim, out_dim, w_tiled, wt_tiled,
+                                                     bias);
     return cudaGetLastError();
 }
 
 cudaError_t forward(const float* x, int rows, int in_dim, int out_dim, const unsigned char* w_tiled,
                     const float* bias, unsigned char* x_tiled, float* ypad, float* y,
-                    unsigned char* saved, int* err, int sm_count, cudaStream_t st) {
+                    unsigned char* saved, unsigned char* zsave, int tile_base, int tile_cap,
+                    int* err, int sm_count, cudaStream_t st) {
     const int n_tiles = (rows + kRows - 1) / kRows;
+    unsigned char* xt = x_tiled + (size_t)tile_base * kInBytes;
     const int total = n_tiles * kRows * kIn;
-    pack_input_kernel<<<(total + 255) / 256, 256, 0, st>>>(x, rows, in_dim, x_tiled, n_tiles);
+    pack_input_kernel<<<(total + 255) / 256, 256, 0, st>>>(x, rows, in_dim, xt, n_tiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = fwd_smem_bytes();
     e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = n_tiles < sm_count ? n_tiles : sm_count;
-    mlp_fwd_kernel<<<grid, kThreads, smem, st>>>(x_tiled, n_tiles, w_tiled, bias, ypad, rows, saved,
-                                                 err);
+    mlp_fwd_kernel<<<grid, kThreads, smem, st>>>(xt, n_tiles, w_tiled, bias, ypad, rows, saved,
+                                                 zsave, tile_base, tile_cap, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     unpack_output_kernel<<<(rows * out_dim + 255) / 256, 256, 0, st>>>(ypad, rows, out_dim, y);
+    return cudaGetLastError();
+}
+
+cudaError_t backward(const float* dy, int rows, int in_dim, int out_dim,
+                     const unsigned char* wt_tiled, const unsigned char* zsave,
+                     unsigned char* dzsave, int tile_base, int tile_cap, float* dx, int* err,
+                     int sm_count, cudaStream_t st) {
+    const int n_tiles = (rows + kRows - 1) / kRows;
+    const size_t smem = fwd_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = n_tiles < sm_count ? n_tiles : sm_count;
+    mlp_bwd_kernel<<<grid, kThreads, smem, st>>>(dy, rows, out_dim, n_tiles, wt_tiled, zsave,
+                                                 dzsave, tile_base, tile_cap, dx, in_dim, err);
+    return cudaGetLastError();
+}
+
+cudaError_t weight_grads(const unsigned char* x_tiled, const unsigned char* saved,
+                         const unsigned char* dzsave, int tile_base, int tile_cap, int rows,
+                         int in_dim, int out_dim, float* grad, cudaStream_t st) {
+    const int chunk = 512;
+    for (int l = 0; l < kLayers; ++l) {
+        const int in_r = l == 0 ? in_dim : kHidden, out_r = l == 3 ? out_dim : kHidden;
+        const unsigned char* a = l == 0 ? x_tiled + (size_t)tile_base * kInBytes
+                                        : saved + ((size_t)l * tile_cap + tile_base) * kActBytes;
+        const size_t a_stride = l == 0 ? kInBytes : kActBytes;
+        const unsigned char* dz = dzsave + ((size_t)l * tile_cap + tile_base) * kActBytes;
+        float* dW = grad + param_offset(l, in_dim, out_dim);
+        const dim3 grid((in_r + 63) / 64, (out_r + 63) / 64, (rows + chunk - 1) / chunk);
+        mlp_dw_kernel<<<grid, 256, 0, st>>>(a, layer_k(l), a_stride, dz, layer_n(l), rows, out_r,
+                                            in_r, chunk, dW);
+        mlp_db_kernel<<<(rows + chunk - 1) / chunk, 256, 0, st>>>(dz, layer_n(l), rows, out_r, chunk,
+                                                                 dW + (size_t)out_r * in_r);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mse(const float* y, const float* t, int n, float* dy, float* loss, cudaStream_t st) {
+    mse_kernel<<<(n + 255) / 256, 256, 0, st>>>(y, t, n, dy, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(float* p, const float* g, float* m, float* v, int n, int step, float lr,
+                 cudaStream_t st) {
+    const float bc1 = 1.f - powf(0.9f, (float)step), bc2 = 1.f - powf(0.999f, (float)step);
+    param_adam_kernel<<<(n + 255) / 256, 256, 0, st>>>(p, g, m, v, n, lr, bc1, bc2);
     return cudaGetLastError();
 }
 
@@ -347,12 +622,16 @@ cudaError_t forward(const float* x, int rows, int in_dim, int out_dim, const uns
 
 // ----------------------------- C ABI ----------------------------------------
 struct stamp_mlp {
-    int in_dim = 0, out_dim = 0, max_rows = 0, sm_count = 0;
+    int in_dim = 0, out_dim = 0, max_rows = 0, train_rows = 0, tile_cap = 0, sm_count = 0;
+    size_t n_params = 0;
     cudaStream_t stream = nullptr;
     char* arena = nullptr;
-    unsigned char *w_tiled = nullptr, *x_tiled = nullptr;
-    float *bias = nullptr, *ypad = nullptr;
+    unsigned char *w_tiled = nullptr, *wt_tiled = nullptr, *x_tiled = nullptr;
+    unsigned char *saved = nullptr, *zsave = nullptr, *dzsave = nullptr;
+    float *bias = nullptr, *ypad = nullptr, *ytrain = nullptr, *dy = nullptr;
+    float *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr, *loss = nullptr;
     int* err = nullptr;
+    int step = 0;
 };
 
 namespace {
@@ -368,34 +647,57 @@ stamp_status mlp_fail(stamp_status s, const char* msg, cudaError_t e = cudaSucce
     stamp::set_last_error(buf);
     return s;
 }
+bool on_device(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+#define MLP_TRY(call, what)                                          \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return mlp_fail(STAMP_ECUDA, what, e_); \
+    } while (0)
 }  // namespace
 
-extern "C" stamp_status stamp_mlp_create(int in_dim, int out_dim, int max_rows, void* cuda_stream,
-                                         stamp_mlp** out) {
+extern "C" stamp_status stamp_mlp_create(int in_dim, int out_dim, int max_rows, int train_rows,
+                                         void* cuda_stream, stamp_mlp** out) {
     using namespace stamp::mlp;
     if (!out) return mlp_fail(STAMP_EINVAL, "out is NULL");
     *out = nullptr;
-    if (in_dim < 1 || in_dim > kIn || out_dim < 1 || out_dim > kOut || max_rows < 1)
-        return mlp_fail(STAMP_EINVAL, "need 1 <= in_dim <= 32, 1 <= out_dim <= 16, max_rows >= 1");
+    if (in_dim < 1 || in_dim > kIn || out_dim < 1 || out_dim > kOut || max_rows < 1 || train_rows < 0)
+        return mlp_fail(STAMP_EINVAL,
+                        "need 1 <= in_dim <= 32, 1 <= out_dim <= 16, max_rows >= 1, train_rows >= 0");
     stamp_mlp* m = new stamp_mlp();
-    m->in_dim = in_dim; m->out_dim = out_dim; m->max_rows = max_rows;
+    m->in_dim = in_dim; m->out_dim = out_dim; m->max_rows = max_rows; m->train_rows = train_rows;
+    m->tile_cap = (train_rows + 127) / 128;
+    m->n_params = param_count(in_dim, out_dim);
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    const size_t tiles = ((size_t)max_rows + 127) / 128;
-    const size_t parts[] = {kWeightBytes, tiles * 128 * kIn * 2, (size_t)kLayers * kHidden * 4,
-                            (size_t)max_rows * kOut * 4, 256};
+    const size_t xt = (size_t)((max_rows > train_rows ? max_rows : train_rows) + 127) / 128;
+    const size_t cap = (size_t)m->tile_cap, np = m->n_params;
+    void** dst[] = {(void**)&m->w_tiled, (void**)&m->wt_tiled, (void**)&m->x_tiled, (void**)&m->bias,
+                    (void**)&m->ypad,    (void**)&m->saved,    (void**)&m->zsave,   (void**)&m->dzsave,
+                    (void**)&m->ytrain,  (void**)&m->dy,       (void**)&m->grad,    (void**)&m->adam_m,
+                    (void**)&m->adam_v,  (void**)&m->loss,     (void**)&m->err};
+    const size_t bytes[] = {kWeightBytes, kWeightBytes, xt * 128 * kIn * 2, (size_t)kLayers * kHidden * 4,
+                            (size_t)max_rows * kOut * 4, 4 * cap * kRows * kHidden * 2,
+                            3 * cap * kRows * kHidden * 2, 4 * cap * kRows * kHidden * 2,
+                            (size_t)train_rows * out_dim * 4, (size_t)train_rows * out_dim * 4,
+                            np * 4, np * 4, np * 4, 4, 4};
     size_t total = 0;
-    for (size_t b : parts) total += (b + 255) / 256 * 256;
+    for (size_t b : bytes) total += (b + 255) / 256 * 256;
     cudaError_t e = cudaMalloc(&m->arena, total);
     if (e != cudaSuccess) { delete m; return mlp_fail(STAMP_ENOMEM, "cudaMalloc failed", e); }
     char* p = m->arena;
-    m->w_tiled = reinterpret_cast<unsigned char*>(p); p += (parts[0] + 255) / 256 * 256;
-    m->x_tiled = reinterpret_cast<unsigned char*>(p); p += (parts[1] + 255) / 256 * 256;
-    m->bias = reinterpret_cast<float*>(p); p += (parts[2] + 255) / 256 * 256;
-    m->ypad = reinterpret_cast<float*>(p); p += (parts[3] + 255) / 256 * 256;
-    m->err = reinterpret_cast<int*>(p);
+    for (size_t q = 0; q < sizeof bytes / sizeof bytes[0]; ++q) {
+        *dst[q] = p;
+        p += (bytes[q] + 255) / 256 * 256;
+    }
     e = cudaMemset(m->arena, 0, total);
     if (e != cudaSuccess) { cudaFree(m->arena); delete m; return mlp_fail(STAMP_ECUDA, "memset failed", e); }
     *out = m;
@@ -414,31 +716,106 @@ extern "C" size_t stamp_mlp_param_count(int in_dim, int out_dim) {
 }
 
 extern "C" stamp_status stamp_mlp_set_params(stamp_mlp* m, const float* params) {
-    if (!m || !params) return mlp_fail(STAMP_EINVAL, "NULL mlp or params");
-    cudaError_t e = stamp::mlp::pack_weights(params, m->in_dim, m->out_dim, m->w_tiled, m->bias,
-                                             m->stream);
-    return e == cudaSuccess ? STAMP_OK : mlp_fail(STAMP_ECUDA, "weight packing failed", e);
+    if (!m || !params || !on_device(params)) return mlp_fail(STAMP_EINVAL, "NULL mlp or non-device params");
+    MLP_TRY(stamp::mlp::pack_weights(params, m->in_dim, m->out_dim, m->w_tiled, m->wt_tiled, m->bias,
+                                     m->stream), "weight packing failed");
+    return STAMP_OK;
 }
 
 extern "C" stamp_status stamp_mlp_forward(stamp_mlp* m, const float* x, int rows, float* y) {
-    if (!m || !x || !y) return mlp_fail(STAMP_EINVAL, "NULL argument");
+    if (!m || !x || !y || !on_device(x) || !on_device(y)) return mlp_fail(STAMP_EINVAL, "NULL or non-device argument");
     if (rows < 1 || rows > m->max_rows) return mlp_fail(STAMP_EINVAL, "rows outside [1, max_rows]");
-    cudaError_t e = stamp::mlp::forward(x, rows, m->in_dim, m->out_dim, m->w_tiled, m->bias,
-                                        m->x_tiled, m->ypad, y, nullptr, m->err, m->sm_count,
-                                        m->stream);
-    return e == cudaSuccess ? STAMP_OK : mlp_fail(STAMP_ECUDA, "MLP forward launch failed", e);
+    MLP_TRY(stamp::mlp::forward(x, rows, m->in_dim, m->out_dim, m->w_tiled, m->bias, m->x_tiled,
+                                m->ypad, y, nullptr, nullptr, 0, 0, m->err, m->sm_count, m->stream),
+            "MLP forward launch failed");
+    return STAMP_OK;
+}
+
+extern "C" stamp_status stamp_mlp_forward_saved(stamp_mlp* m, const float* x, int rows, float* y,
+                                                int tile_base) {
+    if (!m || !x || !y || !on_device(x) || !on_device(y)) return mlp_fail(STAMP_EINVAL, "NULL or non-device argument");
+    const int tiles = (rows + 127) / 128;
+    if (rows < 1 || rows > m->max_rows || tile_base < 0 || tile_base + tiles > m->tile_cap)
+        return mlp_fail(STAMP_EINVAL, "rows / tile_base outside the saved-activation capacity");
+    MLP_TRY(stamp::mlp::forward(x, rows, m->in_dim, m->out_dim, m->w_tiled, m->bias, m->x_tiled,
+                                m->ypad, y, m->saved, m->zsave, tile_base, m->tile_cap, m->err,
+                                m->sm_count, m->stream),
+            "MLP forward launch failed");
+    return STAMP_OK;
+}
+
+extern "C" stamp_status stamp_mlp_backward(stamp_mlp* m, const float* dy, int rows, int tile_base,
+                                           float* dx, float* dparams) {
+    if (!m || !dy || !on_device(dy) || (dx && !on_device(dx)) || (dparams && !on_device(dparams)))
+        return mlp_fail(STAMP_EINVAL, "NULL or non-device argument");
+    const int tiles = (rows + 127) / 128;
+    if (rows < 1 || tile_base < 0 || tile_base + tiles > m->tile_cap)
+        return mlp_fail(STAMP_EINVAL, "rows / tile_base outside the saved-activation capacity");
+    MLP_TRY(stamp::mlp::backward(dy, rows, m->in_dim, m->out_dim, m->wt_tiled, m->zsave, m->dzsave,
+                                 tile_base, m->tile_cap, dx, m->err, m->sm_count, m->stream),
+            "MLP backward launch failed");
+    if (dparams) {
+        MLP_TRY(cudaMemsetAsync(dparams, 0, m->n_params * 4, m->stream), "memset failed");
+        MLP_TRY(stamp::mlp::weight_grads(m->x_tiled, m->saved, m->dzsave, tile_base, m->tile_cap,
+                                         rows, m->in_dim, m->out_dim, dparams, m->stream),
+                "weight-gradient launch failed");
+    }
+    return STAMP_OK;
+}
+
+extern "C" stamp_status stamp_mlp_train(stamp_mlp* m, float* params, const float* x,
+                                        const float* target, int rows, int epochs, int batch,
+                                        float lr, float* loss_out) {
+    if (!m || !params || !x || !target || !on_device(params) || !on_device(x) || !on_device(target))
+        return mlp_fail(STAMP_EINVAL, "NULL or non-device argument");
+    if (batch < 1 || batch > m->train_rows || batch > m->max_rows || rows < batch || epochs < 1)
+        return mlp_fail(STAMP_EINVAL, "need 1 <= batch <= train_rows, rows >= batch, epochs >= 1");
+    const int nb = rows / batch, n = batch * m->out_dim;
+    std::vector<float> losses(epochs);
+    for (int ep = 0; ep < epochs; ++ep) {
+        MLP_TRY(cudaMemsetAsync(m->loss, 0, 4, m->stream), "memset failed");
+        for (int b = 0; b < nb; ++b) {
+            MLP_TRY(stamp::mlp::pack_weights(params, m->in_dim, m->out_dim, m->w_tiled, m->wt_tiled,
+                                             m->bias, m->stream), "weight packing failed");
+            MLP_TRY(stamp::mlp::forward(x + (size_t)b * batch * m->in_dim, batch, m->in_dim, m->out_dim,
+                                        m->w_tiled, m->bias, m->x_tiled, m->ypad, m->ytrain, m->saved,
+                                        m->zsave, 0, m->tile_cap, m->err, m->sm_count, m->stream),
+                    "MLP forward launch failed");
+            MLP_TRY(stamp::mlp::mse(m->ytrain, target + (size_t)b * n, n, m->dy, m->loss, m->stream),
+                    "loss launch failed");
+            MLP_TRY(stamp::mlp::backward(m->dy, batch, m->in_dim, m->out_dim, m->wt_tiled, m->zsave,
+                                         m->dzsave, 0, m->tile_cap, nullptr, m->err, m->sm_count,
+                                         m->stream), "MLP backward launch failed");
+            MLP_TRY(cudaMemsetAsync(m->grad, 0, m->n_params * 4, m->stream), "memset failed");
+            MLP_TRY(stamp::mlp::weight_grads(m->x_tiled, m->saved, m->dzsave, 0, m->tile_cap, batch,
+                                             m->in_dim, m->out_dim, m->grad, m->stream),
+                    "weight-gradient launch failed");
+            MLP_TRY(stamp::mlp::adam(params, m->grad, m->adam_m, m->adam_v, (int)m->n_params,
+                                     ++m->step, lr, m->stream), "Adam launch failed");
+        }
+        float l = 0.f;
+        MLP_TRY(cudaMemcpyAsync(&l, m->loss, 4, cudaMemcpyDeviceToHost, m->stream), "copy failed");
+        MLP_TRY(cudaStreamSynchronize(m->stream), "synchronisation failed");
+        losses[ep] = l / nb;
+    }
+    if (loss_out) std::memcpy(loss_out, losses.data(), epochs * sizeof(float));
+    int f = 0;
+    MLP_TRY(cudaMemcpy(&f, m->err, sizeof f, cudaMemcpyDeviceToHost), "flag read failed");
+    if (f) {
+        cudaMemset(m->err, 0, sizeof(int));
+        return mlp_fail(STAMP_ETIMEOUT, "a bounded device wait of the MLP kernels gave up");
+    }
+    return STAMP_OK;
 }
 
 extern "C" stamp_status stamp_mlp_sync(stamp_mlp* m) {
     if (!m) return mlp_fail(STAMP_EINVAL, "NULL mlp");
-    cudaError_t e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) return mlp_fail(STAMP_ECUDA, "stream synchronisation failed", e);
+    MLP_TRY(cudaStreamSynchronize(m->stream), "stream synchronisation failed");
     int f = 0;
-    e = cudaMemcpy(&f, m->err, sizeof f, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return mlp_fail(STAMP_ECUDA, "flag read failed", e);
+    MLP_TRY(cudaMemcpy(&f, m->err, sizeof f, cudaMemcpyDeviceToHost), "flag read failed");
     if (f) {
         cudaMemset(m->err, 0, sizeof(int));
-        return mlp_fail(STAMP_ETIMEOUT, "a bounded device wait of the MLP kernel gave up");
+        return mlp_fail(STAMP_ETIMEOUT, "a bounded device wait of the MLP kernels gave up");
     }
     return STAMP_OK;
 }

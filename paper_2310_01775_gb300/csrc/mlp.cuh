@@ -35,14 +35,31 @@ __host__ __device__ constexpr size_t param_count(int in_dim, int out_dim) {
 }
 
 size_t fwd_smem_bytes();
+// W_l -> BF16 K-major tiles for the forward (N = out, K = in) and for the
+// input-gradient backward (W_l^T: N = in, K = out), plus FP32 biases.
 cudaError_t pack_weights(const float* params, int in_dim, int out_dim, unsigned char* w_tiled,
-                         float* bias, cudaStream_t st);
-// y (rows x out_dim FP32) = MLP(x (rows x in_dim FP32)).  x_tiled: scratch of
-// ceil(rows/128) * 8 KB; ypad: rows x 16 FP32 scratch; saved: NULL or
-// 4 * ceil(rows/128) * 64 KB for the backward pass.
+                         unsigned char* wt_tiled, float* bias, cudaStream_t st);
+// y (rows x out_dim FP32) = MLP(x (rows x in_dim FP32)).  x_tiled: input
+// tiles (8 KB each, written at tile_base); ypad: rows x 16 FP32 scratch.
+// saved / zsave (NULL or buffers of tile_cap 64 KB tiles per layer) receive
+// the activations for the backward pass at tiles tile_base...
 cudaError_t forward(const float* x, int rows, int in_dim, int out_dim, const unsigned char* w_tiled,
                     const float* bias, unsigned char* x_tiled, float* ypad, float* y,
-                    unsigned char* saved, int* err, int sm_count, cudaStream_t st);
+                    unsigned char* saved, unsigned char* zsave, int tile_base, int tile_cap,
+                    int* err, int sm_count, cudaStream_t st);
+// dx (rows x in_dim, or NULL) from dy (rows x out_dim) for the forward saved at tile_base;
+// dz of every layer goes to dzsave.
+cudaError_t backward(const float* dy, int rows, int in_dim, int out_dim,
+                     const unsigned char* wt_tiled, const unsigned char* zsave,
+                     unsigned char* dzsave, int tile_base, int tile_cap, float* dx, int* err,
+                     int sm_count, cudaStream_t st);
+// grad (packed like the parameters; must be zero) += dL/dW_l, dL/db_l.
+cudaError_t weight_grads(const unsigned char* x_tiled, const unsigned char* saved,
+                         const unsigned char* dzsave, int tile_base, int tile_cap, int rows,
+                         int in_dim, int out_dim, float* grad, cudaStream_t st);
+cudaError_t mse(const float* y, const float* t, int n, float* dy, float* loss, cudaStream_t st);
+cudaError_t adam(float* p, const float* g, float* m, float* v, int n, int step, float lr,
+                 cudaStream_t st);
 
 }  // namespace mlp
 }  // namespace stamp

@@ -58,9 +58,12 @@ _sigs = {
     "stamp_set_lanes": [_vp, _i, _i],
     "stamp_dropped_gradients": [_vp, _vp],
     "stamp_svgd_step_noalloc": [_vp, _vp, _i, _i, _vp, _vp, _i, _f, _i, _vp, _vp, _vp],
-    "stamp_mlp_create": [_i, _i, _i, _vp, ctypes.POINTER(_vp)],
+    "stamp_mlp_create": [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)],
     "stamp_mlp_set_params": [_vp, _vp],
     "stamp_mlp_forward": [_vp, _vp, _i, _vp],
+    "stamp_mlp_forward_saved": [_vp, _vp, _i, _vp, _i],
+    "stamp_mlp_backward": [_vp, _vp, _i, _i, _vp, _vp],
+    "stamp_mlp_train": [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _vp],
     "stamp_mlp_sync": [_vp],
 }
 for _name, _args in _sigs.items():
@@ -253,10 +256,12 @@ class Problem:
 class MLP:
     """The BF16 tensor-core MLP (in_dim -> 256 -> 256 -> 256 -> out_dim, SiLU)."""
 
-    def __init__(self, in_dim: int, out_dim: int, max_rows: int, cuda_stream: int | None = None):
+    def __init__(self, in_dim: int, out_dim: int, max_rows: int, train_rows: int = 0,
+                 cuda_stream: int | None = None):
         self.in_dim, self.out_dim = in_dim, out_dim
         out = _vp()
-        _check(_lib.stamp_mlp_create(in_dim, out_dim, max_rows, cuda_stream, ctypes.byref(out)))
+        _check(_lib.stamp_mlp_create(in_dim, out_dim, max_rows, train_rows, cuda_stream,
+                                     ctypes.byref(out)))
         self.handle = out.value
         self.n_params = int(_lib.stamp_mlp_param_count(in_dim, out_dim))
 
@@ -277,6 +282,22 @@ class MLP:
 
     def forward(self, x, rows, y):
         _check(_lib.stamp_mlp_forward(self.handle, _f32(x, "x"), rows, _f32(y, "y")))
+
+    def forward_saved(self, x, rows, y, tile_base=0):
+        _check(_lib.stamp_mlp_forward_saved(self.handle, _f32(x, "x"), rows, _f32(y, "y"),
+                                            tile_base))
+
+    def backward(self, dy, rows, tile_base=0, dx=None, dparams=None):
+        _check(_lib.stamp_mlp_backward(self.handle, _f32(dy, "dy"), rows, tile_base,
+                                       _f32(dx, "dx"), _f32(dparams, "dparams")))
+
+    def train(self, params, x, target, rows, epochs, batch, lr):
+        """Returns the mean loss of each epoch."""
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(_lib.stamp_mlp_train(self.handle, _f32(params, "params"), _f32(x, "x"),
+                                    _f32(target, "target"), rows, epochs, batch, lr,
+                                    losses.ctypes.data))
+        return losses
 
     def sync(self):
         _check(_lib.stamp_mlp_sync(self.handle))
