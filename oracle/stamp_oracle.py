@@ -343,7 +343,8 @@ def pusher_geometry(q, offset_k, dist_k, P):
 
 
 def simulate(theta, P, init_poses, gumbel=None, hard=False, record=False):
-    """Roll all particles' relaxed plans through H*T substeps.
+    """Roll all particles' relaxed plans through H*T substeps from rest at
+    `init_poses` ((nb, 3) shared, or (N, nb, 3) per particle).
 
     Returns (q, v, z, offset, dist, traj) with traj (N, H*T+1, nb, 6) the state
     before every substep and after the last one when `record` is set.
@@ -353,7 +354,9 @@ def simulate(theta, P, init_poses, gumbel=None, hard=False, record=False):
     H, T = P["H"], P["T"]
     z, offset, dist = relax(theta, P, gumbel, hard)
     nb = P["n_blocks"]
-    q = torch.as_tensor(np.asarray(init_poses, dtype=np.float64), dtype=dt_)[None].expand(N, nb, 3)
+    q0 = torch.as_tensor(np.asarray(init_poses, dtype=np.float64), dtype=dt_)
+    # one start pose set for all particles (nb, 3), or one per particle (N, nb, 3)
+    q = q0.expand(N, nb, 3) if q0.dim() == 3 else q0[None].expand(N, nb, 3)
     v = torch.zeros(N, nb, 3, dtype=dt_)
     traj = []
     for k in range(H):
