@@ -40,7 +40,6 @@ SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes, 1 FMA = 2
 # capture (profiles/rollout_pusher1_h4.md), valid while the kernel source is
 # unchanged (sha256 prefix of csrc/rollout.cuh at capture time).
 TRAFFIC = {("pusher1_h4", "rollout_adj"): ("34b4f045baa4c0c3", 9.997824e6)}
-KERNEL_IDS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init")
 
 
 def peaks():
@@ -141,6 +140,48 @@ def run_reference(args, P, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def surrogate_vs_plain(stream, seeds=(3, 4, 5)):
+    """Time to cost < 1e-3 on planted 3-block problems (H=6, T=100, N=2048):
+    plain SVGD (500 iterations) against the surrogate-assisted solve (surrogate
+    trained on 2^20 simulator transitions; 131072 candidates screened to 2048;
+    300 surrogate + 200 simulator iterations), both stopping at the target
+    (hard simulator check every 10 iterations).  Also the time the surrogate
+    arm needs to reach the cost plain SVGD ends at."""
+    import torch
+    from paper_2310_01775_gb300 import surrogate_compare as SC
+    from paper_2310_01775_gb300 import workloads as W
+    P = W.params("pusher3_h6")
+    sur, train_s, losses = SC.train_surrogate(P, 1 << 20, stream, 131072, P["N"])
+    res = SC.compare(P, seeds, sur, N=P["N"], n_candidates=131072, surrogate_iters=300,
+                     sim_iters=200, stream=stream)
+    # time for the surrogate arm to reach plain SVGD's final cost
+    match = []
+    for row in res["per_seed"]:
+        r = SC.compare(P, (row["seed"],), sur, N=P["N"], n_candidates=131072, surrogate_iters=300,
+                       sim_iters=200, target=row["plain"]["best_cost"] * (1 + 1e-6),
+                       stream=stream)["per_seed"][0]
+        match.append({"seed": row["seed"], "plain_final_cost": row["plain"]["best_cost"],
+                      "plain_seconds": row["plain"]["seconds"],
+                      "surrogate_seconds": r["surrogate"]["seconds"],
+                      "surrogate_iterations": r["surrogate"]["iterations"],
+                      "reached": r["surrogate"]["reached"]})
+    sur.close()
+    arms = {}
+    for arm in ("plain", "surrogate"):
+        rows = [r[arm] for r in res["per_seed"]]
+        arms[arm] = {"reached_target": f"{sum(r['reached'] for r in rows)}/{len(rows)}",
+                     "seconds": [r["seconds"] for r in rows],
+                     "iterations": [r["iterations"] for r in rows],
+                     "best_cost": [r["best_cost"] for r in rows]}
+    return {"problem": "planted 3-block scenes (pusher3_h6 physics; goal = hard rollout of a "
+                       "random plan), N=2048, lr 1e-2, seeds " + ",".join(map(str, seeds)),
+            "target_cost": 1e-3, "surrogate_training": {
+                "transitions": 1 << 20, "seconds": round(train_s, 3),
+                "final_standardized_mse": float(losses[-1])},
+            "plain": arms["plain"], "surrogate": arms["surrogate"],
+            "time_to_plain_final_cost": match}
+
+
 def workload_config(args, P):
     iters = P["svgd_iters"]
     return {"workload": (f"{args.workload}: {P['n_blocks']} block(s), H={P['H']}, T={P['T']}, "
@@ -163,6 +204,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, nargs=2, default=None)
     ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval override")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the surrogate-assisted vs plain SVGD comparison")
     args = ap.parse_args()
 
     from paper_2310_01775_gb300 import workloads as W
@@ -267,13 +310,17 @@ def main():
         v, dt, cores = cpu_oracle_sample(P, init, goal, seed, args.baseline_particles)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.baseline_particles} of {N} particles, 1 iteration ({dt:.1f} s)"}
+    sur = None
+    if world == 1 and not args.no_surrogate:
+        sur = surrogate_vs_plain(stream.cuda_stream)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args, P), "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": int(sum(n for _, n in kt.values())),
-            "kernels_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}}
+            "kernels_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]},
+            "surrogate_vs_plain": sur}
     print(json.dumps(line), flush=True)
     prob.close()
     if world > 1:

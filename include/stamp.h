@@ -176,7 +176,9 @@ enum {
     STAMP_K_ADAM = 5,         /* Adam update */
     STAMP_K_TOPK = 6,         /* sort + distinct plans */
     STAMP_K_INIT = 7,         /* initial particles */
-    STAMP_NKERNELS = 8
+    STAMP_K_SURROGATE = 8,    /* surrogate rollout with its reverse sweep (all its launches) */
+    STAMP_K_SCREEN = 9,       /* candidate generation + surrogate screening (all its launches) */
+    STAMP_NKERNELS = 10
 };
 stamp_status stamp_set_profiling(stamp_problem* prob, int enable);
 /* ms_out, launches_out: host arrays of STAMP_NKERNELS (either may be NULL). */
@@ -253,6 +255,105 @@ stamp_status stamp_mlp_train(stamp_mlp* mlp, float* params, const float* x, cons
                              int rows, int epochs, int batch, float lr, float* loss_out);
 /* Wait for the MLP's stream; STAMP_ETIMEOUT if a bounded device wait gave up. */
 stamp_status stamp_mlp_sync(stamp_mlp* mlp);
+
+/* ---- Surrogate-assisted planning -----------------------------------------
+ * A learned pose-dynamics model of one push (the paper simulates every plan,
+ * Sec. III-B; this model lets the early iterations and the screening of many
+ * candidates skip the simulator).  For push k of a plan:
+ *   f_k = [x_b, y_b, cos phi_b, sin phi_b for each block b] ++ z~_k
+ *         ++ [tanh u_k, sigmoid v_k]                       (8 n_blocks + 2 values)
+ *   q_{k+1} = q_k + MLP(f_k)       (each block's (dx, dy, dphi), world frame)
+ * with z~_k, u_k, v_k the relaxed action of Eq. gamma_map and MLP the network
+ * above (in_dim 8 n_blocks + 2, out_dim 3 n_blocks).  The plan's cost is the
+ * simulator's cost on q_H, and its gradient runs through the H chained
+ * network evaluations (input-gradient MMAs on the tensor cores).
+ * Training transitions: one relaxed push from a random start scene.  With
+ * sm64(k, c) = SplitMix64 output c+1 of a generator started at state k and
+ * U(.) its top 23 bits as ((x >> 41) + 0.5) / 2^23: transition g of `seed`
+ * sits in chunk c0 = g - g mod 4096 (chunk key cs = sm64(seed, c0)) at local
+ * index i.  Start poses: attempt a = 0..31 draws u = U(sm64(sm64(cs, 2),
+ * (32 i + a) * 12 + 3 b + q)) for block b, coordinate q, and sets
+ * x = u - 1/2, y = u - 1/2, phi = (u - 1/2) * 3.14159265 in float32; the
+ * first attempt with all block centres more than 0.16 m apart is taken.
+ * Action: u_j = U(sm64(sm64(cs, 3), i (M + 3) + j)), theta_j = (u_j - 1/2) * 6
+ * for j < M + 2, the M logits multiplied by u_{M+2}.  The push is simulated
+ * with the description's physics (Gumbel noise of seed cs, iteration 0); the
+ * target is each block's pose change. */
+typedef struct stamp_surrogate stamp_surrogate;
+/* desc: the physics of the simulated transitions (n_blocks 1..3; its H is
+ * the longest horizon the surrogate will roll out; T as in the problems it
+ * serves).  max_rows: the largest candidate set to screen (<= 2^20);
+ * max_particles: the largest N of a rollout with gradients.  All device
+ * memory is allocated here (the candidate set, poses and features of
+ * max_rows rows, the MLP's saved activations for H * max_particles rows);
+ * the surrogate runs on cuda_stream. */
+stamp_status stamp_surrogate_create(const stamp_problem_desc* desc, int max_rows,
+                                    int max_particles, void* cuda_stream, stamp_surrogate** out);
+void stamp_surrogate_destroy(stamp_surrogate* s);
+/* Network input and output widths; returns the packed parameter count. */
+int stamp_surrogate_dims(const stamp_surrogate* s, int* in_dim, int* out_dim);
+/* Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases from the
+ * counter generator with key `seed` (draw t = index in the packed vector). */
+stamp_status stamp_surrogate_init_params(stamp_surrogate* s, unsigned long long seed);
+/* params: device, packed as for stamp_mlp_set_params. */
+stamp_status stamp_surrogate_set_params(stamp_surrogate* s, const float* params);
+stamp_status stamp_surrogate_get_params(stamp_surrogate* s, float* params);
+/* The first n transitions of `seed`: x_out (device n x in_dim) features,
+ * y_out (device n x 3 n_blocks) pose changes.  Asynchronous. */
+stamp_status stamp_surrogate_transitions(stamp_surrogate* s, int n, unsigned long long seed,
+                                         float* x_out, float* y_out);
+/* Train the surrogate's own parameters on n transitions (device x: n x in_dim,
+ * y: n x out_dim).  Transitions in which a block moved more than 0.5 m or
+ * turned more than pi (blow-ups of the explicit contact integration) are
+ * dropped; the targets are standardized per output (mean, standard
+ * deviation over the kept rows); Adam (lr) minimises the mean squared error
+ * in standardized units over `epochs` passes of consecutive minibatches of
+ * `batch` rows (batch <= max(16384, H * max_particles rounded up to 128));
+ * then the scaling is folded back into the output layer, so the parameters
+ * always predict pose changes in metres and radians.  loss_out: host, the
+ * mean standardized loss of each epoch, or NULL.  Allocates its scratch
+ * (about (in_dim + out_dim) * 4 bytes per transition) for the call; waits
+ * for the stream. */
+stamp_status stamp_surrogate_train(stamp_surrogate* s, const float* x, const float* y, int n,
+                                   int epochs, int batch, float lr, float* loss_out);
+/* Transitions the last stamp_surrogate_train call kept. */
+int stamp_surrogate_last_kept(const stamp_surrogate* s);
+/* Surrogate cost (device N) of the plans theta (device N x D) of problem p
+ * (its scene, goal, horizon and relaxation; same n_blocks), Gumbel noise of
+ * (seed, iter) as in stamp_rollout_fwd (iter < 0: none), and, when
+ * grad_logp (device N x D) is given, -dC/dtheta (N <= max_particles; without
+ * it N <= max_rows).  Asynchronous on the surrogate's stream. */
+stamp_status stamp_surrogate_rollout(stamp_surrogate* s, stamp_problem* p, const float* theta,
+                                     int N, unsigned long long seed, int iter, float* cost,
+                                     float* grad_logp);
+/* The N candidates (device n_candidates x D) of lowest noise-free surrogate
+ * cost, ties to the lower index, in ascending cost order: theta_out (device
+ * N x D) and their indices (device N ints, or NULL).  N <= 4096. */
+stamp_status stamp_surrogate_screen(stamp_surrogate* s, stamp_problem* p, const float* candidates,
+                                    int n_candidates, int N, float* theta_out, int* index_out);
+/* Wait for the surrogate's stream; STAMP_ETIMEOUT if a bounded device wait gave up. */
+stamp_status stamp_surrogate_sync(stamp_surrogate* s);
+/* Algorithm 1 with the surrogate: n_candidates >= N particles drawn as in
+ * stamp_solve (theta ~ U(-1,1)^D from seed; the first N are stamp_solve's
+ * start), the N of lowest noise-free surrogate cost kept (n_candidates == N:
+ * all, in order), then surrogate_iters SVGD iterations on the surrogate's
+ * gradients, sim_iters SVGD iterations and sgd_iters plain-gradient
+ * iterations on the simulator's (Adam's step count runs on), then the hard
+ * evaluation and top-k of stamp_solve.  stats_out: host, minimum relaxed
+ * cost of each iteration (the surrogate's cost in its iterations), or NULL.
+ * p and s must run on the same stream; N <= max_particles of both, and
+ * N <= 4096 when screening. */
+stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_candidates, int N,
+                                   int surrogate_iters, int sim_iters, int sgd_iters,
+                                   unsigned long long seed, float lr, float* theta_out,
+                                   float* cost_out, int k, int* topk_particle, float* stats_out);
+/* Early stop for stamp_solve and stamp_solve_surrogate: every check_every
+ * iterations (0: never) the particles are rolled out hard on the simulator
+ * without noise and the solve ends when the lowest cost is below
+ * target_cost.  stamp_solve_info reports the iterations the last solve ran
+ * and the lowest hard cost of its last check (or of the final evaluation). */
+stamp_status stamp_set_target(stamp_problem* prob, float target_cost, int check_every);
+stamp_status stamp_solve_info(stamp_problem* prob, int* iterations_run, float* best_hard_cost);
 
 /* Static text of a status code, and the last error message of this thread. */
 const char* stamp_status_str(stamp_status s);

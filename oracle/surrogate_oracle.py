@@ -20,7 +20,7 @@ written here in torch float64 so that reverse mode gives -dC/dtheta.
 
 Training transitions (one push from a random scene; the pose samplers are
 counter-based SplitMix64 draws, the same definitions the CUDA sampler uses):
-    transition g lives in chunk c0 = g - g mod 16384 with local index i; the
+    transition g lives in chunk c0 = g - g mod 4096 with local index i; the
     chunk key is cs = sm64(seed, c0).
     start poses: key sm64(cs, 2); attempt a = 0..31 draws
         u_{b,q} = U(sm64(key, (32 i + a) * 12 + 3 b + q))
@@ -29,8 +29,10 @@ counter-based SplitMix64 draws, the same definitions the CUDA sampler uses):
     centres are all more than 0.16 m apart (dx*dx + dy*dy > 0.16*0.16, each
     product and the sum rounded to float32) is taken; if none is, attempt 31
     with x_b = -0.4 + 0.8 b / max(n_b - 1, 1).
-    action: key sm64(cs, 3); theta_j = (U(sm64(key, i P + j)) - 1/2) * 6 in
-    float32, j < P = M + 2 (logits, offset and distance parameters).
+    action: key sm64(cs, 3); u_j = U(sm64(key, i (P + 1) + j)) for j <= P
+    (P = M + 2); theta_j = (u_j - 1/2) * 6 in float32 for j < P, and the M
+    logits are further multiplied by u_P, so the choice weights range from
+    nearly uniform to nearly one-hot (each product rounded to float32).
     push: the simulator's one-action rollout (H = 1) from the start poses at
     rest, Gumbel noise of seed cs, iteration 0; the target is the pose change
     q_final - q_start.
@@ -42,7 +44,7 @@ import torch
 
 from . import stamp_oracle as O
 
-CHUNK = 16384
+CHUNK = 4096
 STREAM_POSES, STREAM_ACTIONS = 2, 3
 MAX_BLOCKS = 4          # pose draws are laid out for up to four blocks per attempt
 ATTEMPTS = 32
@@ -96,8 +98,11 @@ def sample_start_poses(cs: int, m: int, nb: int) -> np.ndarray:
 def sample_actions(cs: int, m: int, Pn: int) -> np.ndarray:
     """(m, Pn) float32 action parameters of one chunk, in [-3, 3]."""
     key = O.sm64(np.uint64(cs), STREAM_ACTIONS)
-    u = O.uniform23(O.sm64(key, np.arange(m * Pn, dtype=np.uint64))).astype(np.float32)
-    return ((u - np.float32(0.5)) * np.float32(6.0)).reshape(m, Pn)
+    ctr = np.arange(m * (Pn + 1), dtype=np.uint64).reshape(m, Pn + 1)
+    u = O.uniform23(O.sm64(key, ctr)).astype(np.float32)
+    th = (u[:, :Pn] - np.float32(0.5)) * np.float32(6.0)
+    th[:, :Pn - 2] *= u[:, Pn:]
+    return th
 
 
 def transitions(seed: int, n: int, P: dict, dtype=torch.float64):

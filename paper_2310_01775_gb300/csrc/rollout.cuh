@@ -409,6 +409,11 @@ __global__ void __launch_bounds__(128) rollout_fwd_kernel(const SimConst sc, con
     make_corners(cn, lane);
     Blocks<NB> s;
     init_state(sc, s);
+    if (a.init_states) {   // per-particle start poses (transition sampling)
+        const float* p0 = a.init_states + (size_t)i * 3 * NB;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) { s.x[b] = p0[3 * b]; s.y[b] = p0[3 * b + 1]; s.ph[b] = p0[3 * b + 2]; }
+    }
     float dsum = 0.f;
     const size_t ck_stride = (size_t)a.N * S;   // floats per checkpoint
     float2* tape_i = reinterpret_cast<float2*>(a.tape + (size_t)i * S);

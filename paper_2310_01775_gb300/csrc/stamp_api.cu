@@ -55,7 +55,7 @@ struct stamp_problem {
     char* arena = nullptr;
     float *tape = nullptr, *cost = nullptr, *grad = nullptr, *theta = nullptr, *m = nullptr,
           *v = nullptr, *phi = nullptr, *d2 = nullptr, *h = nullptr, *one = nullptr;
-    unsigned *hist = nullptr, *stats = nullptr, *sel = nullptr, *counter = nullptr;
+    unsigned *hist = nullptr, *stats = nullptr, *sel = nullptr, *counter = nullptr, *stop = nullptr;
     int *flag = nullptr, *topk = nullptr;
     unsigned long long* dropped = nullptr;
     // last forward
@@ -64,6 +64,11 @@ struct stamp_problem {
     unsigned long long last_seed = 0;
     const float* last_theta = nullptr;
     int fwd_lanes = 0, adj_lanes = 0;
+    // early stop of the solves, and what the last solve did
+    float target = 0.f;
+    int check_every = 0;
+    int iters_run = 0;
+    float best_hard = 0.f;
     // kernel timing
     bool prof = false;
     std::vector<cudaEvent_t> ev;          // pairs (start, stop)
@@ -134,10 +139,12 @@ stamp_status check_dev(const void* ptr, const char* name, bool allow_null = fals
     } while (0)
 
 stamp_status fwd(stamp_problem* p, const float* theta, int N, unsigned long long seed, int iter,
-                 int hard, float* cost, float* final_state, unsigned* stats_word) {
+                 int hard, float* cost, float* final_state, unsigned* stats_word,
+                 const float* init_states = nullptr) {
     stamp::RolloutArgs a{};
     a.theta = theta; a.N = N; a.seed = seed; a.iter = iter; a.hard = hard;
     a.tape = p->tape; a.cost = cost; a.final_state = final_state; a.stats_min = stats_word;
+    a.init_states = init_states;
     const int lanes = lanes_for(p, N, false);
     STAMP_TRY(timed(p, STAMP_K_ROLLOUT_FWD,
                     [&] { return stamp::launch_rollout_fwd(p->sc, a, lanes, p->stream); }));
@@ -190,6 +197,114 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
     });
 }
 
+// Iterations of one solve: [0, sur) on the surrogate's gradients, then svgd
+// Stein iterations and sgd plain-gradient iterations on the simulator.
+struct Phases {
+    stamp_surrogate* s;
+    int n_cand, sur, svgd, sgd;
+};
+
+// Events around a multi-launch piece (surrogate rollout, screening).
+template <class F>
+stamp_status timed_piece(stamp_problem* p, int kind, F&& piece) {
+    const bool rec = p->prof && p->ev_used < p->ev_kind.size();
+    if (rec) STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used], p->stream));
+    STAMP_TRY(piece());
+    if (rec) {
+        STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used + 1], p->stream));
+        p->ev_kind[p->ev_used++] = kind;
+    }
+    return STAMP_OK;
+}
+
+// Hard, noise-free rollout of all particles; the lowest cost in *best.
+stamp_status hard_min(stamp_problem* p, const float* th, int N, unsigned long long seed, float* cost,
+                      float* best) {
+    STAMP_CUDA(cudaMemsetAsync(p->stop, 0xFF, sizeof(unsigned), p->stream));
+    STAMP_TRY(fwd(p, th, N, seed, -1, 1, cost, nullptr, p->stop));
+    unsigned bits = 0;
+    STAMP_CUDA(cudaMemcpyAsync(&bits, p->stop, sizeof bits, cudaMemcpyDeviceToHost, p->stream));
+    STAMP_CUDA(cudaStreamSynchronize(p->stream));
+    std::memcpy(best, &bits, sizeof bits);
+    return STAMP_OK;
+}
+
+stamp_status run_solve(stamp_problem* p, const Phases& ph, int N, unsigned long long seed, float lr,
+                       const float* theta_init, float* theta_out, float* cost_out, int k,
+                       int* topk_particle, float* stats_out) {
+    STAMP_TRY(check_n(p, N));
+    if (ph.svgd < 0 || ph.sgd < 0) return fail(STAMP_EINVAL, "negative iteration count");
+    const long long iters = (long long)ph.sur + ph.svgd + ph.sgd;
+    if (stats_out && iters > kMaxStatsIters)
+        return fail(STAMP_EINVAL, "stats_out supports at most %lld iterations", kMaxStatsIters);
+    if (!theta_out) return fail(STAMP_EINVAL, "theta_out is NULL");
+    if (k < 0 || (k > 0 && !topk_particle)) return fail(STAMP_EINVAL, "bad k / topk_particle");
+    if (k > 0 && N > stamp::kMaxTopkN) return fail(STAMP_EINVAL, "top-k needs N <= %d", stamp::kMaxTopkN);
+    if (k > N) return fail(STAMP_EINVAL, "k=%d > N=%d", k, N);
+    if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
+    const int D = p->sc.D;
+    const size_t nd = (size_t)N * D;
+    const bool out_dev = is_device_ptr(theta_out);
+    float* th = out_dev ? theta_out : p->theta;
+    if (ph.s && ph.n_cand > N) {
+        float* cand = stamp::surrogate_candidates(ph.s);
+        STAMP_TRY(timed_piece(p, STAMP_K_SCREEN, [&] {
+            const cudaError_t e = stamp::launch_init_theta(cand, ph.n_cand, D, seed, p->stream);
+            if (e != cudaSuccess) return fail(STAMP_ECUDA, "candidate launch failed: %s", cudaGetErrorString(e));
+            return stamp::surrogate_screen(ph.s, p->sc, cand, ph.n_cand, N, th, nullptr);
+        }));
+    } else if (theta_init) {
+        STAMP_CUDA(cudaMemcpyAsync(th, theta_init, nd * sizeof(float), cudaMemcpyDefault, p->stream));
+    } else {
+        STAMP_TRY(timed(p, STAMP_K_INIT, [&] { return stamp::launch_init_theta(th, N, D, seed, p->stream); }));
+    }
+    STAMP_CUDA(cudaMemsetAsync(p->m, 0, nd * sizeof(float), p->stream));
+    STAMP_CUDA(cudaMemsetAsync(p->v, 0, nd * sizeof(float), p->stream));
+    if (stats_out) STAMP_CUDA(cudaMemsetAsync(p->stats, 0xFF, iters * sizeof(unsigned), p->stream));
+    p->iters_run = (int)iters;
+    p->best_hard = INFINITY;
+    for (long long it = 0; it < iters; ++it) {
+        unsigned* sw = stats_out ? p->stats + it : nullptr;
+        if (it < ph.sur) {
+            STAMP_TRY(timed_piece(p, STAMP_K_SURROGATE, [&] {
+                return stamp::surrogate_rollout(ph.s, p->sc, th, N, seed, (int)it, p->cost, p->grad, sw);
+            }));
+        } else {
+            STAMP_TRY(fwd(p, th, N, seed, (int)it, 0, p->cost, nullptr, sw));
+            STAMP_TRY(adj(p, th, N, p->grad));
+        }
+        STAMP_TRY(svgd(p, th, p->grad, N, p->m, p->v, (int)it + 1, lr,
+                       it >= (long long)ph.sur + ph.svgd ? 1 : 0, nullptr, nullptr));
+        if (p->check_every > 0 && (it + 1) % p->check_every == 0) {
+            STAMP_TRY(hard_min(p, th, N, seed, p->cost, &p->best_hard));
+            if (p->best_hard < p->target) {
+                p->iters_run = (int)(it + 1);
+                break;
+            }
+        }
+    }
+    // hard evaluation (Gamma, no noise) and the distinct-plan top-k
+    float* ch = (cost_out && is_device_ptr(cost_out)) ? cost_out : p->cost;
+    STAMP_CUDA(cudaMemsetAsync(p->stop, 0xFF, sizeof(unsigned), p->stream));
+    STAMP_TRY(fwd(p, th, N, seed, -1, 1, ch, nullptr, p->stop));
+    if (k > 0)
+        STAMP_TRY(timed(p, STAMP_K_TOPK, [&] { return stamp::launch_topk(th, ch, N, p->sc, k, p->topk, p->stream); }));
+    if (!out_dev)
+        STAMP_CUDA(cudaMemcpyAsync(theta_out, th, nd * sizeof(float), cudaMemcpyDefault, p->stream));
+    if (cost_out && ch != cost_out)
+        STAMP_CUDA(cudaMemcpyAsync(cost_out, ch, N * sizeof(float), cudaMemcpyDefault, p->stream));
+    if (k > 0)
+        STAMP_CUDA(cudaMemcpyAsync(topk_particle, p->topk, k * sizeof(int), cudaMemcpyDefault, p->stream));
+    if (stats_out)
+        STAMP_CUDA(cudaMemcpyAsync(stats_out, p->stats, iters * sizeof(float), cudaMemcpyDefault, p->stream));
+    unsigned bits = 0;
+    STAMP_CUDA(cudaMemcpyAsync(&bits, p->stop, sizeof bits, cudaMemcpyDeviceToHost, p->stream));
+    STAMP_CUDA(cudaStreamSynchronize(p->stream));
+    std::memcpy(&p->best_hard, &bits, sizeof bits);
+    STAMP_TRY(collect(p));
+    return check_flag(p);
+}
+
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
 bool finite_nonneg(float x) { return std::isfinite(x) && x >= 0.f; }
 
@@ -198,6 +313,14 @@ bool finite_nonneg(float x) { return std::isfinite(x) && x >= 0.f; }
 namespace stamp {
 
 void set_last_error(const char* msg) { g_err = msg; }
+
+SimConst problem_const(const stamp_problem* p) { return p->sc; }
+
+stamp_status rollout_from(stamp_problem* p, const float* theta, const float* init_states, int N,
+                          uint64_t seed, int iter, float* cost, float* final_state) {
+    STAMP_TRY(check_n(p, N));
+    return fwd(p, theta, N, seed, iter, 0, cost, final_state, nullptr, init_states);
+}
 
 bool lanes_supported(int nb, int lanes) {
     switch (nb) {
@@ -331,6 +454,7 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         {(void**)&p->dropped, sizeof(unsigned long long)},
         {(void**)&p->sel, 4 * sizeof(unsigned)},
         {(void**)&p->counter, 3 * sizeof(unsigned)},
+        {(void**)&p->stop, sizeof(unsigned)},
     };
     size_t total = 0;
     for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
@@ -431,49 +555,42 @@ stamp_status stamp_solve(stamp_problem* p, int N, int svgd_iters, int sgd_iters,
                          float* theta_out, float* cost_out, int k, int* topk_particle,
                          float* stats_out) {
     if (!p) return fail(STAMP_EINVAL, "NULL problem");
-    STAMP_TRY(check_n(p, N));
-    if (svgd_iters < 0 || sgd_iters < 0) return fail(STAMP_EINVAL, "negative iteration count");
-    const long long iters = (long long)svgd_iters + sgd_iters;
-    if (stats_out && iters > kMaxStatsIters)
-        return fail(STAMP_EINVAL, "stats_out supports at most %lld iterations", kMaxStatsIters);
-    if (!theta_out) return fail(STAMP_EINVAL, "theta_out is NULL");
-    if (k < 0 || (k > 0 && !topk_particle)) return fail(STAMP_EINVAL, "bad k / topk_particle");
-    if (k > 0 && N > stamp::kMaxTopkN) return fail(STAMP_EINVAL, "top-k needs N <= %d", stamp::kMaxTopkN);
-    if (k > N) return fail(STAMP_EINVAL, "k=%d > N=%d", k, N);
-    if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
-    const int D = p->sc.D;
-    const size_t nd = (size_t)N * D;
-    const bool out_dev = is_device_ptr(theta_out);
-    float* th = out_dev ? theta_out : p->theta;
-    if (theta_init)
-        STAMP_CUDA(cudaMemcpyAsync(th, theta_init, nd * sizeof(float), cudaMemcpyDefault, p->stream));
-    else
-        STAMP_TRY(timed(p, STAMP_K_INIT, [&] { return stamp::launch_init_theta(th, N, D, seed, p->stream); }));
-    STAMP_CUDA(cudaMemsetAsync(p->m, 0, nd * sizeof(float), p->stream));
-    STAMP_CUDA(cudaMemsetAsync(p->v, 0, nd * sizeof(float), p->stream));
-    if (stats_out) STAMP_CUDA(cudaMemsetAsync(p->stats, 0xFF, iters * sizeof(unsigned), p->stream));
-    for (long long it = 0; it < iters; ++it) {
-        STAMP_TRY(fwd(p, th, N, seed, (int)it, 0, p->cost, nullptr, stats_out ? p->stats + it : nullptr));
-        STAMP_TRY(adj(p, th, N, p->grad));
-        STAMP_TRY(svgd(p, th, p->grad, N, p->m, p->v, (int)it + 1, lr, it >= svgd_iters ? 1 : 0,
-                       nullptr, nullptr));
-    }
-    // hard evaluation (Gamma, no noise) and the distinct-plan top-k
-    float* ch = (cost_out && is_device_ptr(cost_out)) ? cost_out : p->cost;
-    STAMP_TRY(fwd(p, th, N, seed, -1, 1, ch, nullptr, nullptr));
-    if (k > 0)
-        STAMP_TRY(timed(p, STAMP_K_TOPK, [&] { return stamp::launch_topk(th, ch, N, p->sc, k, p->topk, p->stream); }));
-    if (!out_dev)
-        STAMP_CUDA(cudaMemcpyAsync(theta_out, th, nd * sizeof(float), cudaMemcpyDefault, p->stream));
-    if (cost_out && ch != cost_out)
-        STAMP_CUDA(cudaMemcpyAsync(cost_out, ch, N * sizeof(float), cudaMemcpyDefault, p->stream));
-    if (k > 0)
-        STAMP_CUDA(cudaMemcpyAsync(topk_particle, p->topk, k * sizeof(int), cudaMemcpyDefault, p->stream));
-    if (stats_out)
-        STAMP_CUDA(cudaMemcpyAsync(stats_out, p->stats, iters * sizeof(float), cudaMemcpyDefault, p->stream));
-    STAMP_CUDA(cudaStreamSynchronize(p->stream));
-    STAMP_TRY(collect(p));
-    return check_flag(p);
+    Phases ph{nullptr, 0, 0, svgd_iters, sgd_iters};
+    return run_solve(p, ph, N, seed, lr, theta_init, theta_out, cost_out, k, topk_particle, stats_out);
+}
+
+stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_candidates, int N,
+                                   int surrogate_iters, int sim_iters, int sgd_iters,
+                                   unsigned long long seed, float lr, float* theta_out,
+                                   float* cost_out, int k, int* topk_particle, float* stats_out) {
+    if (!p || !s) return fail(STAMP_EINVAL, "NULL problem or surrogate");
+    if (stamp::surrogate_stream(s) != p->stream)
+        return fail(STAMP_EINVAL, "the problem and the surrogate must share one stream");
+    if (N > stamp::surrogate_max_particles(s))
+        return fail(STAMP_EINVAL, "N=%d exceeds the surrogate's max_particles", N);
+    if (n_candidates < N || n_candidates > stamp::surrogate_max_rows(s))
+        return fail(STAMP_EINVAL, "need N <= n_candidates <= the surrogate's max_rows");
+    if (n_candidates > N && N > stamp::kMaxScreenN)
+        return fail(STAMP_EINVAL, "screening keeps at most %d particles", stamp::kMaxScreenN);
+    if (surrogate_iters < 0 || sim_iters < 0 || sgd_iters < 0)
+        return fail(STAMP_EINVAL, "negative iteration count");
+    Phases ph{s, n_candidates, surrogate_iters, sim_iters, sgd_iters};
+    return run_solve(p, ph, N, seed, lr, nullptr, theta_out, cost_out, k, topk_particle, stats_out);
+}
+
+stamp_status stamp_set_target(stamp_problem* p, float target_cost, int check_every) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    if (check_every < 0 || !std::isfinite(target_cost)) return fail(STAMP_EINVAL, "bad target or interval");
+    p->target = target_cost;
+    p->check_every = check_every;
+    return STAMP_OK;
+}
+
+stamp_status stamp_solve_info(stamp_problem* p, int* iterations_run, float* best_hard_cost) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    if (iterations_run) *iterations_run = p->iters_run;
+    if (best_hard_cost) *best_hard_cost = p->best_hard;
+    return STAMP_OK;
 }
 
 stamp_status stamp_sync(stamp_problem* p) {

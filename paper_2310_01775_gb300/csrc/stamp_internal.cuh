@@ -8,12 +8,15 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "stamp.h"
+
 namespace stamp {
 
 constexpr int kMaxBlocks = 4;     // n_blocks <= 4  ->  M = 4*n_blocks <= 16 choices
 constexpr int kMaxH = 16;         // plan codes pack 4 bits per action into 64 bits
 constexpr int kMaxTopkN = 8192;   // single-CTA bitonic sort of (cost, index)
 constexpr int kMaxShares = 8;     // partial Stein directions summed by the Adam kernel
+constexpr int kMaxScreenN = 4096; // particles kept by one surrogate screening
 
 // Problem constants in the form the kernels use (derived once on the host).
 struct SimConst {
@@ -39,6 +42,7 @@ struct RolloutArgs {
     unsigned* stats_min;    // one word, atomicMin of cost bits, or NULL
     float* grad;            // N x D (adjoint): grad log rho = -dC/dtheta
     unsigned long long* dropped;   // count of particles whose reverse sweep overflowed
+    const float* init_states;      // N x n_blocks x 3 initial poses (at rest), or NULL: the scene's
 };
 
 // ---------------------------------------------------------------------------
@@ -95,6 +99,22 @@ cudaError_t launch_adam(float* theta, const float* part, int shares, float* phi_
 cudaError_t launch_init_theta(float* theta, int N, int D, uint64_t seed, cudaStream_t st);
 cudaError_t launch_topk(const float* theta, const float* cost, int N, const SimConst& sc, int k,
                         int* topk_out, cudaStream_t st);
+
+// Problem constants of a problem object, and a forward rollout (timed like
+// the solve's) from per-particle start poses (N x n_blocks x 3, at rest).
+SimConst problem_const(const stamp_problem* p);
+stamp_status rollout_from(stamp_problem* p, const float* theta, const float* init_states, int N,
+                          uint64_t seed, int iter, float* cost, float* final_state);
+
+// Surrogate pieces (surrogate.cu) used by the surrogate-assisted solve.
+stamp_status surrogate_rollout(stamp_surrogate* s, const SimConst& sc, const float* theta, int N,
+                               uint64_t seed, int iter, float* cost, float* grad, unsigned* stats_word);
+stamp_status surrogate_screen(stamp_surrogate* s, const SimConst& sc, const float* cand, int n_cand,
+                              int N, float* theta_out, int* index_out);
+float* surrogate_candidates(stamp_surrogate* s);
+int surrogate_max_rows(const stamp_surrogate* s);
+int surrogate_max_particles(const stamp_surrogate* s);
+cudaStream_t surrogate_stream(const stamp_surrogate* s);
 
 // Text returned by stamp_last_error() on the calling thread.
 void set_last_error(const char* msg);

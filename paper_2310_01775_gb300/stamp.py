@@ -21,7 +21,8 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 STAMP_OK, STAMP_EINVAL, STAMP_ENOMEM, STAMP_ECUDA, STAMP_ENONFINITE, STAMP_ETIMEOUT = range(6)
-KERNELS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init")
+KERNELS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init",
+           "surrogate", "screen")
 STAMP_NKERNELS = len(KERNELS)
 
 
@@ -65,6 +66,19 @@ _sigs = {
     "stamp_mlp_backward": [_vp, _vp, _i, _i, _vp, _vp],
     "stamp_mlp_train": [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _vp],
     "stamp_mlp_sync": [_vp],
+    "stamp_surrogate_create": [ctypes.POINTER(stamp_problem_desc), _i, _i, _vp, ctypes.POINTER(_vp)],
+    "stamp_surrogate_init_params": [_vp, _ull],
+    "stamp_surrogate_set_params": [_vp, _vp],
+    "stamp_surrogate_get_params": [_vp, _vp],
+    "stamp_surrogate_transitions": [_vp, _i, _ull, _vp, _vp],
+    "stamp_surrogate_train": [_vp, _vp, _vp, _i, _i, _i, _f, _vp],
+    "stamp_surrogate_rollout": [_vp, _vp, _vp, _i, _ull, _i, _vp, _vp],
+    "stamp_surrogate_screen": [_vp, _vp, _vp, _i, _i, _vp, _vp],
+    "stamp_surrogate_sync": [_vp],
+    "stamp_surrogate_dims": [_vp, _vp, _vp],
+    "stamp_solve_surrogate": [_vp, _vp, _i, _i, _i, _i, _i, _ull, _f, _vp, _vp, _i, _vp, _vp],
+    "stamp_set_target": [_vp, _f, _i],
+    "stamp_solve_info": [_vp, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -73,6 +87,10 @@ _lib.stamp_mlp_destroy.argtypes = [_vp]
 _lib.stamp_mlp_destroy.restype = None
 _lib.stamp_mlp_param_count.argtypes = [_i, _i]
 _lib.stamp_mlp_param_count.restype = ctypes.c_size_t
+_lib.stamp_surrogate_last_kept.argtypes = [_vp]
+_lib.stamp_surrogate_last_kept.restype = ctypes.c_int
+_lib.stamp_surrogate_destroy.argtypes = [_vp]
+_lib.stamp_surrogate_destroy.restype = None
 _lib.stamp_problem_destroy.argtypes = [_vp]
 _lib.stamp_problem_destroy.restype = None
 _lib.stamp_status_str.argtypes = [ctypes.c_int]
@@ -251,6 +269,92 @@ class Problem:
 
     def dropped_gradients(self):
         return stamp_dropped_gradients(self.handle)
+
+    def solve_surrogate(self, surrogate, n_candidates, N, surrogate_iters, sim_iters, seed, lr,
+                        theta_out, cost_out=None, k=0, topk_particle=None, stats_out=None,
+                        sgd_iters=0):
+        """Algorithm 1 with screening and surrogate iterations (stamp_solve_surrogate)."""
+        if topk_particle is not None and str(topk_particle.dtype) not in ("int32", "torch.int32"):
+            raise TypeError("topk_particle must be int32")
+        self._tape_owner = None
+        _check(_lib.stamp_solve_surrogate(self.handle, surrogate.handle, n_candidates, N,
+                                          surrogate_iters, sim_iters, sgd_iters, seed, lr,
+                                          _f32(theta_out, "theta_out"), _f32(cost_out, "cost_out"),
+                                          k, _ptr(topk_particle), _f32(stats_out, "stats_out")))
+
+    def set_target(self, target_cost, check_every):
+        """Early stop of the solves on the lowest hard, noise-free simulator cost."""
+        _check(_lib.stamp_set_target(self.handle, target_cost, check_every))
+
+    def solve_info(self):
+        """(iterations the last solve ran, lowest hard cost of its last check)."""
+        it, best = ctypes.c_int(), ctypes.c_float()
+        _check(_lib.stamp_solve_info(self.handle, ctypes.byref(it), ctypes.byref(best)))
+        return it.value, best.value
+
+
+class Surrogate:
+    """Learned pose-dynamics surrogate of one push (stamp_surrogate_*)."""
+
+    def __init__(self, params: dict, max_rows: int, max_particles: int,
+                 cuda_stream: int | None = None):
+        out = _vp()
+        _check(_lib.stamp_surrogate_create(ctypes.byref(stamp_problem_desc.from_params(params)),
+                                           max_rows, max_particles, cuda_stream, ctypes.byref(out)))
+        self.handle = out.value
+        i, o = ctypes.c_int(), ctypes.c_int()
+        self.n_params = _lib.stamp_surrogate_dims(self.handle, ctypes.byref(i), ctypes.byref(o))
+        self.in_dim, self.out_dim = i.value, o.value
+
+    def close(self):
+        if self.handle:
+            _lib.stamp_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_params(self, seed):
+        _check(_lib.stamp_surrogate_init_params(self.handle, seed))
+
+    def set_params(self, params):
+        _check(_lib.stamp_surrogate_set_params(self.handle, _f32(params, "params")))
+
+    def get_params(self, params):
+        _check(_lib.stamp_surrogate_get_params(self.handle, _f32(params, "params")))
+
+    def transitions(self, n, seed, x_out, y_out):
+        _check(_lib.stamp_surrogate_transitions(self.handle, n, seed, _f32(x_out, "x_out"),
+                                                _f32(y_out, "y_out")))
+
+    def train(self, x, y, n, epochs, batch, lr):
+        """Returns the mean loss of each epoch."""
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(_lib.stamp_surrogate_train(self.handle, _f32(x, "x"), _f32(y, "y"), n, epochs,
+                                          batch, lr, losses.ctypes.data))
+        return losses
+
+    def last_kept(self):
+        """Transitions the last train() call kept (blow-ups dropped)."""
+        return int(_lib.stamp_surrogate_last_kept(self.handle))
+
+    def rollout(self, problem, theta, N, seed, iter, cost, grad_logp=None):
+        _check(_lib.stamp_surrogate_rollout(self.handle, problem.handle, _f32(theta, "theta"), N,
+                                            seed, iter, _f32(cost, "cost"),
+                                            _f32(grad_logp, "grad_logp")))
+
+    def screen(self, problem, candidates, n_candidates, N, theta_out, index_out=None):
+        if index_out is not None and str(index_out.dtype) not in ("int32", "torch.int32"):
+            raise TypeError("index_out must be int32")
+        _check(_lib.stamp_surrogate_screen(self.handle, problem.handle,
+                                           _f32(candidates, "candidates"), n_candidates, N,
+                                           _f32(theta_out, "theta_out"), _ptr(index_out)))
+
+    def sync(self):
+        _check(_lib.stamp_surrogate_sync(self.handle))
 
 
 class MLP:

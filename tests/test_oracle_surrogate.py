@@ -115,9 +115,17 @@ def test_start_pose_sampler_ranges_separation_and_moments():
 
 
 def test_action_sampler_range_and_moments():
+    """Offset and distance parameters U(-3, 3) (variance 3); logits U(-3, 3)
+    times a per-row U(0, 1) scale: variance 3 E[w^2] = 1, and one row's
+    logits share that scale."""
     th = SO.sample_actions(123, 5000, 6).astype(np.float64)
     assert th.shape == (5000, 6) and np.abs(th).max() <= 3.0
-    assert abs(th.mean()) < 0.05 and abs(th.var() - 3.0) < 0.1
+    assert abs(th.mean()) < 0.05
+    assert abs(th[:, 4:].var() - 3.0) < 0.15 and abs(th[:, :4].var() - 1.0) < 0.06
+    cs = 123
+    key = O.sm64(np.uint64(cs), SO.STREAM_ACTIONS)
+    w = O.uniform23(O.sm64(key, np.arange(5000, dtype=np.uint64) * 7 + 6))
+    assert (np.abs(th[:, :4]).max(1) <= 3.0 * w + 1e-6).all()
 
 
 def test_transition_targets_are_simulator_pose_changes():
