@@ -103,6 +103,15 @@ stamp_status stamp_rollout_fwd(stamp_problem* prob, const float* theta, int N,
                                unsigned long long seed, int iter, int hard, float* cost,
                                float* final_state);
 
+/* stamp_rollout_fwd from per-particle start poses: init_states (device,
+ * N x n_blocks x 3: x, y, yaw per block, at rest) replaces the scene's start
+ * poses (e.g. replanning from the current state, or simulating
+ * transitions).  The tape it keeps serves stamp_rollout_adjoint only for the
+ * gradient with respect to theta at these start poses. */
+stamp_status stamp_rollout_fwd_from(stamp_problem* prob, const float* theta,
+                                    const float* init_states, int N, unsigned long long seed,
+                                    int iter, int hard, float* cost, float* final_state);
+
 /* Reverse sweep (Sec. III-B: gradients back-propagated through the whole
  * trajectory) of the last stamp_rollout_fwd, recomputing the substeps between
  * checkpoints.  theta, N, seed and iter must be those of that call

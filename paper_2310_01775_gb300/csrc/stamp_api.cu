@@ -511,6 +511,18 @@ stamp_status stamp_rollout_fwd(stamp_problem* p, const float* theta, int N, unsi
     return fwd(p, theta, N, seed, iter, hard ? 1 : 0, cost, final_state, nullptr);
 }
 
+stamp_status stamp_rollout_fwd_from(stamp_problem* p, const float* theta, const float* init_states,
+                                    int N, unsigned long long seed, int iter, int hard, float* cost,
+                                    float* final_state) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_n(p, N));
+    STAMP_TRY(check_dev(theta, "theta"));
+    STAMP_TRY(check_dev(init_states, "init_states"));
+    STAMP_TRY(check_dev(cost, "cost"));
+    STAMP_TRY(check_dev(final_state, "final_state", true));
+    return fwd(p, theta, N, seed, iter, hard ? 1 : 0, cost, final_state, nullptr, init_states);
+}
+
 stamp_status stamp_rollout_adjoint(stamp_problem* p, const float* theta, int N,
                                    unsigned long long seed, int iter, float* grad_logp) {
     if (!p) return fail(STAMP_EINVAL, "NULL problem");

@@ -1,10 +1,14 @@
 """One stamp_solve of a named workload, for profiler captures.
 
     python -m paper_2310_01775_gb300.profile_case pusher1_h4 20
+    python -m paper_2310_01775_gb300.profile_case surrogate 20
 
 Builds the workload's problem (seed 0 scene), runs `iters` SVGD iterations
 plus the hard evaluation and top-3 on the current CUDA device, and prints the
 best hard cost.  Small iteration counts keep an ncu capture short.
+`surrogate`: the 3-block workload's surrogate-assisted solve (a surrogate
+trained for one epoch on 2^16 transitions; 131072 candidates screened to
+2048; `iters` surrogate iterations, then 2 on the simulator).
 """
 from __future__ import annotations
 
@@ -17,7 +21,31 @@ from paper_2310_01775_gb300 import stamp as S
 from paper_2310_01775_gb300 import workloads as W
 
 
+def surrogate_case(iters: int) -> float:
+    P = W.params("pusher3_h6")
+    stream = torch.cuda.current_stream().cuda_stream
+    init, goal = W.scene(P, 0)
+    N = P["N"]
+    sur = S.Surrogate(P, 131072, N, stream)
+    n = 1 << 16
+    x = torch.empty(n, sur.in_dim, device="cuda")
+    y = torch.empty(n, sur.out_dim, device="cuda")
+    sur.transitions(n, 1, x, y)
+    sur.init_params(2)
+    sur.train(x, y, n, 1, 4096, 2e-3)
+    prob = S.Problem(P, init, goal, N, stream)
+    theta = torch.empty(N, prob.D, device="cuda")
+    cost = torch.empty(N, device="cuda")
+    prob.solve_surrogate(sur, 131072, N, iters, 2, 0, 1e-2, theta, cost)
+    torch.cuda.synchronize()
+    prob.close()
+    sur.close()
+    return float(cost.min())
+
+
 def main(name: str = "pusher1_h4", iters: int = 2) -> float:
+    if name == "surrogate":
+        return surrogate_case(iters)
     P = W.params(name)
     init, goal = W.scene(P, 0)
     N = P["N"]

@@ -50,6 +50,7 @@ _sigs = {
                              ctypes.POINTER(_vp)],
     "stamp_rollout_fwd": [_vp, _vp, _i, _ull, _i, _i, _vp, _vp],
     "stamp_rollout_adjoint": [_vp, _vp, _i, _ull, _i, _vp],
+    "stamp_rollout_fwd_from": [_vp, _vp, _vp, _i, _ull, _i, _i, _vp, _vp],
     "stamp_read_tape": [_vp, _i, _vp],
     "stamp_svgd_step": [_vp, _vp, _vp, _i, _vp, _vp, _i, _f, _i, _vp, _vp],
     "stamp_solve": [_vp, _i, _i, _i, _ull, _f, _vp, _vp, _vp, _i, _vp, _vp],
@@ -237,6 +238,14 @@ class Problem:
     def rollout_fwd(self, theta, N, seed, iter, hard, cost, final_state=None):
         self._tape_owner = None          # the tape now belongs to this call
         stamp_rollout_fwd(self.handle, theta, N, seed, iter, hard, cost, final_state)
+
+    def rollout_fwd_from(self, theta, init_states, N, seed, iter, hard, cost, final_state=None):
+        """Forward rollout from per-particle start poses (N x n_blocks x 3)."""
+        self._tape_owner = None
+        _check(_lib.stamp_rollout_fwd_from(self.handle, _f32(theta, "theta"),
+                                           _f32(init_states, "init_states"), N, seed, iter,
+                                           int(hard), _f32(cost, "cost"),
+                                           _f32(final_state, "final_state")))
 
     def rollout_adjoint(self, theta, N, seed, iter, grad_logp):
         stamp_rollout_adjoint(self.handle, theta, N, seed, iter, grad_logp)

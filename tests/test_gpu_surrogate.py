@@ -3,8 +3,8 @@
 
 Bars.  Transition features: sampled poses bit-exact (same float32 operations
 on both sides), derived features within 2e-6; simulated pose changes within
-the trajectory bar 1e-4 on conditioned transitions (float32 floor, and the
-FP64 response to a one-ulp change of theta, both below 1e-5).  Surrogate cost and gradient: the network runs in bfloat16 (8
+the trajectory bar 1e-4 on conditioned transitions (two float32 replays, one
+from start poses moved by an ulp, within 1e-5 of FP64 over the whole push).  Surrogate cost and gradient: the network runs in bfloat16 (8
 significant bits, unit roundoff 2^-9); a bias-only network removes the
 bfloat16 products and must match the closed form to float32 rounding, while
 a random network is held to a median relative error of 2e-2 (cost) and 3e-2
@@ -67,18 +67,24 @@ def test_transitions_match_the_oracle():
     M = 12
     gum = np.concatenate([O.gumbel_noise(cs, 0, m, 1, M) for _, m, cs in SO._chunks(seed, n)])
     th64, q64 = th.astype(np.float64), q0.astype(np.float64)
-    _, f64 = O.rollout(th64, P1, q64, np.zeros((3, 3)), gum)
-    _, f32 = O.rollout(th64, P1, q64, np.zeros((3, 3)), gum, dtype=torch.float32)
-    # a second probe of the conditioning: FP64 again with theta moved by about
-    # one float32 ulp (relative 2^-23, fixed signs)
-    sgn = np.where(np.random.default_rng(0).random(th64.shape) < 0.5, -1.0, 1.0)
-    _, f64p = O.rollout(th64 * (1 + sgn * 2.0 ** -23), P1, q64, np.zeros((3, 3)), gum)
+    _, f64, t64 = O.rollout(th64, P1, q64, np.zeros((3, 3)), gum, record=True)
     want = f64[:, :, :3].reshape(n, 9)
-    rel = lambda a: np.abs(a[:, :, :3].reshape(n, 9) - want).max(1) / np.abs(want).max(1)
-    floor, probe = rel(f32), rel(f64p)
+    scale = np.abs(want).max(1)
+
+    def traj_floor(init):
+        """Largest pose deviation from FP64 over the whole push, of a float32 replay."""
+        _, _, t = O.rollout(th64, P1, init, np.zeros((3, 3)), gum, record=True, dtype=torch.float32)
+        return np.abs(t[..., :3] - t64[..., :3]).reshape(n, -1).max(1) / scale
+
+    # conditioning: float32 replays stay within 1e-5 of FP64 over the whole push,
+    # also from start poses moved by about one float32 ulp (fixed random signs);
+    # squeezed blocks can diverge mid-push and re-converge at rest, so the end
+    # pose alone does not show it
+    sgn = np.where(np.random.default_rng(0).random(q64.shape) < 0.5, -1.0, 1.0)
+    floor, probe = traj_floor(q64), traj_floor(q64 * (1 + sgn * 2.0 ** -23))
     got = q0.reshape(n, 9).astype(np.float64) + y
-    err = np.abs(got - want).max(1) / np.abs(want).max(1)
-    ok = (floor < 1e-5) & (probe < 1e-5)   # squeezed blocks amplify rounding
+    err = np.abs(got - want).max(1) / scale
+    ok = (floor < 1e-5) & (probe < 1e-5)
     stats = (f"conditioned {ok.mean():.3f}, max err there {err[ok].max(initial=0):.2e}, "
              f"median err {np.median(err):.2e}, median floor {np.median(floor):.2e}")
     assert ok.mean() > 0.5, stats
