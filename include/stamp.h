@@ -364,6 +364,65 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
 stamp_status stamp_set_target(stamp_problem* prob, float target_cost, int check_every);
 stamp_status stamp_solve_info(stamp_problem* prob, int* iterations_run, float* best_hard_cost);
 
+/* ---- Batched serving --------------------------------------------------------
+ * Many planning problems solved together (Algorithm 1 on each), for serving
+ * uneven requests on one GPU.  All instances share the physics (T, dt,
+ * contact, friction, tau, cost weights) and differ in block count, horizon,
+ * particle count, scene and seed.  Per Stein iteration the batch issues one
+ * forward and one adjoint launch per block-count class, one launch each for
+ * the pairwise distances, the two median digits, the Stein direction and
+ * Adam over all instances, and a counter bump; iterations between early-stop
+ * checks are captured once in a CUDA graph and replayed.  Each instance
+ * computes what stamp_solve computes for it alone with the same lanes and
+ * checkpoint interval (its particles start from the same draws). */
+typedef struct stamp_batch stamp_batch;
+typedef struct {
+    int n_blocks, H, N;            /* 1..4 blocks, 1..16 actions, 1..8192 particles */
+    unsigned long long seed;       /* initial particles and Gumbel noise, as stamp_solve's seed */
+    float init[12];                /* n_blocks x (x, y, yaw) start poses (rest unused) */
+    float goal[12];                /* n_blocks x (x, y, yaw) goal poses */
+} stamp_instance_desc;
+/* physics: shared constants (its n_blocks, H and ckpt_every are ignored);
+ * inst: host array of n_instances (<= 4096).  Allocates everything the
+ * solves need (particles, Adam moments, tapes with room for any checkpoint
+ * interval, N x N distances per instance, work-item tables); the solves run
+ * on a stream of the batch's own after waiting for cuda_stream. */
+stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_instance_desc* inst,
+                                int n_instances, void* cuda_stream, stamp_batch** out);
+void stamp_batch_destroy(stamp_batch* batch);
+/* Launch configuration of one block-count class: lanes per particle (as
+ * stamp_set_lanes), CTA size (32..128, a multiple of 32; particles per CTA =
+ * cta / lanes) and checkpoint interval (divides T). */
+stamp_status stamp_batch_set_config(stamp_batch* batch, int n_blocks, int lanes, int cta,
+                                    int ckpt_every);
+stamp_status stamp_batch_get_config(stamp_batch* batch, int n_blocks, int* lanes, int* cta,
+                                    int* ckpt_every);
+/* Autotuner: per class, times `reps` forward + adjoint launches for each
+ * supported lane count, CTA size 64/128 and checkpoint interval 1/5/25 on
+ * the solve's initial particles, and keeps the fastest.  Waits. */
+stamp_status stamp_batch_autotune(stamp_batch* batch, int reps);
+/* Algorithm 1 (SVGD phase) on every instance for up to `iters` (<= 65536)
+ * iterations at Adam rate lr.  check_every > 0: every check_every iterations
+ * all running instances are rolled out hard without noise and an instance
+ * whose lowest cost is below target_cost stops (its particles freeze).
+ * use_graph: replay the captured iterations (0: launch them one by one; the
+ * results are the same).  Ends with the hard evaluation and distinct top-3
+ * of every instance.  Waits for completion; STAMP_ENONFINITE / ETIMEOUT as
+ * stamp_solve. */
+stamp_status stamp_batch_solve(stamp_batch* batch, int iters, float lr, float target_cost,
+                               int check_every, int use_graph);
+/* Results of the last solve (host arrays of n_instances, any may be NULL):
+ * iterations run, lowest hard cost at the end, seconds from the solve's
+ * start to the check that stopped the instance (-1: not stopped), the top-3
+ * particle indices (3 per instance, -1 padded); units = particle-substeps
+ * advanced forward and back (N H T per running instance per iteration),
+ * seconds = the solve's wall time. */
+stamp_status stamp_batch_results(stamp_batch* batch, int* iterations, float* best_cost,
+                                 double* seconds_to_target, int* top3, long long* units,
+                                 double* seconds);
+/* Copy one instance's particles (N x D) to host or device memory. */
+stamp_status stamp_batch_read_theta(stamp_batch* batch, int instance, float* theta_out);
+
 /* Static text of a status code, and the last error message of this thread. */
 const char* stamp_status_str(stamp_status s);
 const char* stamp_last_error(void);

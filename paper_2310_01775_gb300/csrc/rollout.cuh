@@ -393,14 +393,12 @@ __device__ __forceinline__ void init_state(const SimConst& sc, Blocks<NB>& s) {
 __device__ __forceinline__ float wrapf(float e) { return atan2f(sinf(e), cosf(e)); }
 
 // ------------------------------ forward kernel -------------------------------
+// One team's forward rollout of particle i (on = false: a surplus team that
+// shadows particle i and stores nothing).
 template <int NB, int L>
-__global__ void __launch_bounds__(128) rollout_fwd_kernel(const SimConst sc, const RolloutArgs a) {
+__device__ __forceinline__ void fwd_team(const SimConst& sc, const RolloutArgs& a, int i, bool on,
+                                         int lane) {
     constexpr int M = Dims<NB>::M, S = Dims<NB>::S;
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = gtid & (L - 1);
-    int i = gtid / L;
-    const bool on = i < a.N;
-    if (!on) i = a.N - 1;   // surplus teams shadow the last particle, store nothing
     const float* th = a.theta + (size_t)i * sc.D;
     const bool noise = a.iter >= 0;
     const uint64_t gkey = noise ? sm64(sm64(a.seed, kStreamGumbel), (uint64_t)a.iter) : 0ull;
@@ -454,6 +452,68 @@ __global__ void __launch_bounds__(128) rollout_fwd_kernel(const SimConst sc, con
     }
     if (on && a.final_state)
         store_state<NB, L>(reinterpret_cast<float2*>(a.final_state + (size_t)i * S), s, lane, true);
+}
+
+template <int NB, int L>
+__global__ void __launch_bounds__(128) rollout_fwd_kernel(const SimConst sc, const RolloutArgs a) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = gtid / L;
+    const bool on = i < a.N;
+    if (!on) i = a.N - 1;   // surplus teams shadow the last particle, store nothing
+    fwd_team<NB, L>(sc, a, i, on, gtid & (L - 1));
+}
+
+// Batched launch: team t -> (instance, particle) through the instances' first
+// teams (warp aligned, so a warp never mixes instances); the instance's
+// horizon, scene and buffers replace the class-wide constants.  Teams of
+// stopped instances return at once.
+template <int NB>
+__device__ __forceinline__ bool batch_team(const SimConst& sc0, const BatchArgs& b, int t,
+                                           SimConst& sc, RolloutArgs& a, int& i, bool& on) {
+    if (t >= b.n_teams) return false;
+    int lo = 0, hi = b.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&b.inst[mid].team0) <= t) lo = mid; else hi = mid - 1;
+    }
+    const BatchInst* in = b.inst + lo;
+    if (!__ldg(&b.active[in->gid])) return false;
+    sc = sc0;
+    sc.H = in->H;
+    sc.D = in->D;
+    sc.n_ckpt = in->n_ckpt;
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sc.init[q][c] = in->init[q][c];
+            sc.goal[q][c] = in->goal[q][c];
+        }
+    a = RolloutArgs{};
+    a.theta = in->theta;
+    a.N = in->N;
+    a.seed = in->seed;
+    a.iter = b.iter_dev ? *b.iter_dev : b.iter;
+    a.hard = b.hard;
+    a.tape = in->tape;
+    a.cost = in->cost;
+    a.grad = in->grad;
+    a.dropped = b.dropped;
+    i = t - in->team0;
+    on = i < in->N;
+    if (!on) i = in->N - 1;
+    return true;
+}
+
+template <int NB, int L>
+__global__ void __launch_bounds__(128) rollout_fwd_batch_kernel(const SimConst sc0, const BatchArgs b) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    SimConst sc;
+    RolloutArgs a;
+    int i;
+    bool on;
+    if (!batch_team<NB>(sc0, b, gtid / L, sc, a, i, on)) return;
+    fwd_team<NB, L>(sc, a, i, on, gtid & (L - 1));
 }
 
 // ------------------------------ adjoint pieces -------------------------------
@@ -721,14 +781,10 @@ __device__ __forceinline__ void substep_vjp(const SimConst& sc, const Blocks<NB>
 // Shared memory: per team, C states (before each substep of the current
 // segment), stride C*S/2 + 1 float2 to spread teams over banks.
 template <int NB, int L>
-__global__ void __launch_bounds__(128) rollout_adj_kernel(const SimConst sc, const RolloutArgs a) {
+__device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& a, int i, bool on,
+                                         int lane) {
     constexpr int M = Dims<NB>::M, P = Dims<NB>::P, S = Dims<NB>::S, SP = Slots<NB, L>::SP;
     extern __shared__ float2 seg_smem[];
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = gtid & (L - 1);
-    int i = gtid / L;
-    const bool on = i < a.N;
-    if (!on) i = a.N - 1;
     const int team = threadIdx.x / L;
     const int seg_stride = sc.C * (S / 2) + 1;
     float2* seg = seg_smem + (size_t)team * seg_stride;
@@ -880,6 +936,26 @@ __global__ void __launch_bounds__(128) rollout_adj_kernel(const SimConst sc, con
     }
 }
 
+template <int NB, int L>
+__global__ void __launch_bounds__(128) rollout_adj_kernel(const SimConst sc, const RolloutArgs a) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = gtid / L;
+    const bool on = i < a.N;
+    if (!on) i = a.N - 1;
+    adj_team<NB, L>(sc, a, i, on, gtid & (L - 1));
+}
+
+template <int NB, int L>
+__global__ void __launch_bounds__(128) rollout_adj_batch_kernel(const SimConst sc0, const BatchArgs b) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    SimConst sc;
+    RolloutArgs a;
+    int i;
+    bool on;
+    if (!batch_team<NB>(sc0, b, gtid / L, sc, a, i, on)) return;
+    adj_team<NB, L>(sc, a, i, on, gtid & (L - 1));
+}
+
 // ------------------------------ launch --------------------------------------
 template <int NB, int L>
 cudaError_t launch(const SimConst& sc, const RolloutArgs& a, bool adjoint, cudaStream_t st) {
@@ -899,6 +975,28 @@ cudaError_t launch(const SimConst& sc, const RolloutArgs& a, bool adjoint, cudaS
             if (e != cudaSuccess) return e;
         }
         rollout_adj_kernel<NB, L><<<grid, cta, smem, st>>>(sc, a);
+    }
+    return cudaGetLastError();
+}
+
+// Batched launch of one block-count class: b.n_teams teams of L lanes in
+// CTAs of `cta` threads (a multiple of 32).
+template <int NB, int L>
+cudaError_t launch_batch(const SimConst& sc, const BatchArgs& b, int cta, bool adjoint, cudaStream_t st) {
+    const long long threads_total = (long long)b.n_teams * L;
+    const int grid = (int)((threads_total + cta - 1) / cta);
+    if (grid < 1) return cudaSuccess;
+    if (!adjoint) {
+        rollout_fwd_batch_kernel<NB, L><<<grid, cta, 0, st>>>(sc, b);
+    } else {
+        const size_t smem = (size_t)(cta / L) * (sc.C * (Dims<NB>::S / 2) + 1) * sizeof(float2);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(rollout_adj_batch_kernel<NB, L>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        rollout_adj_batch_kernel<NB, L><<<grid, cta, smem, st>>>(sc, b);
     }
     return cudaGetLastError();
 }

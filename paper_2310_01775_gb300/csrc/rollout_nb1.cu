@@ -13,4 +13,14 @@ cudaError_t launch_rollout_nb1(const SimConst& sc, const RolloutArgs& a, int lan
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_rollout_batch_nb1(const SimConst& sc, const BatchArgs& b, int lanes, int cta,
+                                        bool adjoint, cudaStream_t st) {
+    switch (lanes) {
+        case 1: return rollout::launch_batch<1, 1>(sc, b, cta, adjoint, st);
+        case 2: return rollout::launch_batch<1, 2>(sc, b, cta, adjoint, st);
+        case 4: return rollout::launch_batch<1, 4>(sc, b, cta, adjoint, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace stamp

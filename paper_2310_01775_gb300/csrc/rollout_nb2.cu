@@ -14,4 +14,15 @@ cudaError_t launch_rollout_nb2(const SimConst& sc, const RolloutArgs& a, int lan
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_rollout_batch_nb2(const SimConst& sc, const BatchArgs& b, int lanes, int cta,
+                                        bool adjoint, cudaStream_t st) {
+    switch (lanes) {
+        case 2: return rollout::launch_batch<2, 2>(sc, b, cta, adjoint, st);
+        case 4: return rollout::launch_batch<2, 4>(sc, b, cta, adjoint, st);
+        case 8: return rollout::launch_batch<2, 8>(sc, b, cta, adjoint, st);
+        case 16: return rollout::launch_batch<2, 16>(sc, b, cta, adjoint, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace stamp

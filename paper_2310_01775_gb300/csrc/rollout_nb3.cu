@@ -13,4 +13,14 @@ cudaError_t launch_rollout_nb3(const SimConst& sc, const RolloutArgs& a, int lan
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_rollout_batch_nb3(const SimConst& sc, const BatchArgs& b, int lanes, int cta,
+                                        bool adjoint, cudaStream_t st) {
+    switch (lanes) {
+        case 8: return rollout::launch_batch<3, 8>(sc, b, cta, adjoint, st);
+        case 16: return rollout::launch_batch<3, 16>(sc, b, cta, adjoint, st);
+        case 32: return rollout::launch_batch<3, 32>(sc, b, cta, adjoint, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace stamp

@@ -45,6 +45,30 @@ struct RolloutArgs {
     const float* init_states;      // N x n_blocks x 3 initial poses (at rest), or NULL: the scene's
 };
 
+// One problem instance of a batch, as the batched rollout kernels see it.
+struct BatchInst {
+    const float* theta;     // N x D, this instance's rows of the batch's particles
+    float* grad;            // N x D
+    float* tape;            // (n_ckpt + 1) x N x S
+    float* cost;            // N
+    int N, H, D, n_ckpt;
+    int team0;              // first team of the instance in its class launch (warp aligned)
+    int gid;                // index in the batch (active flags)
+    unsigned long long seed;
+    float init[kMaxBlocks][3];
+    float goal[kMaxBlocks][3];
+};
+struct BatchArgs {
+    const BatchInst* inst;  // the class's instances, ascending team0
+    int n_inst;
+    int n_teams;            // teams of the launch (a multiple of the teams per warp)
+    const int* active;      // per batch instance: 0 = stopped (its teams return at once)
+    const int* iter_dev;    // iteration number on the device (graph replays), or NULL
+    int iter;               // iteration when iter_dev is NULL (< 0: no noise)
+    int hard;
+    unsigned long long* dropped;
+};
+
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator: output
 // number ctr+1 of the generator started at state `key` is mix(key+(ctr+1)*G).
@@ -69,6 +93,14 @@ cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lan
 cudaError_t launch_rollout_adj(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st);
 bool lanes_supported(int nb, int lanes);
 int default_lanes(int nb, int N, bool adjoint);
+
+// Batched launchers (rollout_nb*.cu): cta threads per CTA, a multiple of 32.
+cudaError_t launch_rollout_batch(int nb, const SimConst& sc, const BatchArgs& b, int lanes, int cta,
+                                 bool adjoint, cudaStream_t st);
+cudaError_t launch_rollout_batch_nb1(const SimConst&, const BatchArgs&, int, int, bool, cudaStream_t);
+cudaError_t launch_rollout_batch_nb2(const SimConst&, const BatchArgs&, int, int, bool, cudaStream_t);
+cudaError_t launch_rollout_batch_nb3(const SimConst&, const BatchArgs&, int, int, bool, cudaStream_t);
+cudaError_t launch_rollout_batch_nb4(const SimConst&, const BatchArgs&, int, int, bool, cudaStream_t);
 
 // Per-NB launchers defined in rollout_nb*.cu.
 cudaError_t launch_rollout_nb1(const SimConst&, const RolloutArgs&, int, bool, cudaStream_t);
@@ -97,6 +129,38 @@ cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, cons
 cudaError_t launch_adam(float* theta, const float* part, int shares, float* phi_out, float* m,
                         float* v, int n_elems, int step, float lr, int* flag, cudaStream_t st);
 cudaError_t launch_init_theta(float* theta, int N, int D, uint64_t seed, cudaStream_t st);
+
+// Batched Stein step pieces (svgd.cu): one launch covers every instance of a
+// batch through per-CTA work items; CTAs of stopped instances return at once.
+struct SvgdInst {
+    const float* theta;     // N x D (16-byte aligned)
+    const float* grad;      // N x D (16-byte aligned)
+    float* d2;              // N x N
+    unsigned* hist;         // 2048 + 2048 + 1024 (zeroed before the pairwise launch)
+    unsigned* sel;          // 4
+    unsigned* counter;      // 3, zero between launches
+    float* h;               // bandwidth
+    float* part;            // shares x N x D
+    int N, D;
+    int nt;                 // pairwise tiles per side
+    int med_ctas;           // CTAs of each median-digit pass
+    int shares, j_chunk;    // Stein-sum split (as for one problem of N particles)
+    int gid;                // index in the batch (active flags)
+    long long elem0;        // first element of the instance in the concatenated particles
+};
+cudaError_t launch_pairwise_batch(const SvgdInst* inst, const int4* items, int n_items, int max_D,
+                                  const int* active, cudaStream_t st);
+cudaError_t launch_median_digit_batch(const SvgdInst* inst, const int2* items, int n_items,
+                                      const int* active, int digit, cudaStream_t st);
+cudaError_t launch_phi_batch(const SvgdInst* inst, const int4* items, int n_items, int max_D,
+                             const int* active, int* err, cudaStream_t st);
+// step_dev: Adam steps taken so far; bc[s] = (1 - 0.9^s, 1 - 0.999^s).
+cudaError_t launch_adam_batch(float* theta, float* m, float* v, long long n, const SvgdInst* inst,
+                              int n_inst, const int* active, const int* step_dev, const float2* bc,
+                              float lr, int* flag, cudaStream_t st);
+// The single-problem Stein-sum split for N particles, and rows per phi CTA.
+void phi_batch_plan(int N, int* shares, int* j_chunk);
+int phi_rows_per_block();
 cudaError_t launch_topk(const float* theta, const float* cost, int N, const SimConst& sc, int k,
                         int* topk_out, cudaStream_t st);
 

@@ -19,6 +19,9 @@ namespace {
 
 constexpr int kTile = 32;                      // pairwise tile edge
 constexpr int kBins0 = 2048, kBins1 = 2048, kBins2 = 1024;
+// static shared memory of the pairwise kernel (digit-0 histogram, mirror
+// tile, the bin search's scratch), with margin
+constexpr size_t kPairwiseStatic = kBins0 * 4 + kTile * (kTile + 1) * 4 + 256;
 
 __device__ __forceinline__ unsigned digit_of(unsigned bits, int d) {
     return d == 0 ? (bits >> 21) : d == 1 ? ((bits >> 10) & 2047u) : (bits & 1023u);
@@ -89,14 +92,11 @@ __device__ bool last_block(unsigned* counter, unsigned total) {
 
 // d2 for one upper-triangle tile pair (bi <= bj), mirrored into the lower
 // triangle; histogram of digit 0 over i < j.  The last CTA picks digit 0.
-__global__ void __launch_bounds__(256) pairwise_kernel(const float* __restrict__ theta, int N,
-                                                       int D, float* __restrict__ d2,
-                                                       unsigned* __restrict__ hist,
-                                                       unsigned* __restrict__ sel,
-                                                       unsigned* __restrict__ counter,
-                                                       float* __restrict__ h_dev) {
-    const int bi = blockIdx.y, bj = blockIdx.x;
-    if (bi > bj) return;
+__device__ __forceinline__ void pairwise_body(const float* __restrict__ theta, int N, int D,
+                                              float* __restrict__ d2, unsigned* __restrict__ hist,
+                                              unsigned* __restrict__ sel,
+                                              unsigned* __restrict__ counter,
+                                              float* __restrict__ h_dev, int bi, int bj, int nt) {
     extern __shared__ float sm[];
     const int ld = D + 1;                        // padded rows: conflict-free column walks
     float* A = sm;
@@ -139,8 +139,7 @@ __global__ void __launch_bounds__(256) pairwise_kernel(const float* __restrict__
         }
     for (int t = threadIdx.x; t < kBins0; t += blockDim.x)
         if (h0[t]) atomicAdd(&hist[t], h0[t]);
-    const unsigned nt = gridDim.x;
-    if (last_block(counter, nt * (nt + 1) / 2)) {
+    if (last_block(counter, (unsigned)(nt * (nt + 1) / 2))) {
         if (N < 2) {
             if (threadIdx.x == 0) *h_dev = 1.f;
             return;
@@ -151,15 +150,34 @@ __global__ void __launch_bounds__(256) pairwise_kernel(const float* __restrict__
     }
 }
 
+__global__ void __launch_bounds__(256) pairwise_kernel(const float* __restrict__ theta, int N,
+                                                       int D, float* __restrict__ d2,
+                                                       unsigned* __restrict__ hist,
+                                                       unsigned* __restrict__ sel,
+                                                       unsigned* __restrict__ counter,
+                                                       float* __restrict__ h_dev) {
+    if (blockIdx.y > blockIdx.x) return;
+    pairwise_body(theta, N, D, d2, hist, sel, counter, h_dev, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// Batched: one CTA per work item (instance, tile row bi, tile column bj >= bi).
+__global__ void __launch_bounds__(256) pairwise_batch_kernel(const SvgdInst* __restrict__ inst,
+                                                             const int4* __restrict__ items,
+                                                             const int* __restrict__ active) {
+    const int4 it = items[blockIdx.x];
+    const SvgdInst& g = inst[it.x];
+    if (!active[g.gid]) return;
+    pairwise_body(g.theta, g.N, g.D, g.d2, g.hist, g.sel, g.counter, g.h, it.y, it.z, g.nt);
+}
+
 // Histogram of digit `dg` (1 or 2) over the i<j entries whose higher digits
 // match the prefix chosen so far; rows of the upper triangle, grid-strided.
-__global__ void __launch_bounds__(256) median_digit_kernel(int N, int dg,
-                                                           const float* __restrict__ d2,
-                                                           unsigned* __restrict__ hist,
-                                                           unsigned* __restrict__ sel,
-                                                           unsigned* __restrict__ counter,
-                                                           float* __restrict__ h_dev,
-                                                           float* __restrict__ h_out) {
+__device__ __forceinline__ void median_digit_body(int N, int dg, const float* __restrict__ d2,
+                                                  unsigned* __restrict__ hist,
+                                                  unsigned* __restrict__ sel,
+                                                  unsigned* __restrict__ counter,
+                                                  float* __restrict__ h_dev,
+                                                  float* __restrict__ h_out, int cta, int ctas) {
     __shared__ unsigned hloc[kBins1];
     const unsigned b0 = __ldcg(sel), b1 = dg == 2 ? __ldcg(sel + 2) : 0u;
     const unsigned prefix = dg == 1 ? b0 : ((b0 << 11) | b1);
@@ -167,7 +185,7 @@ __global__ void __launch_bounds__(256) median_digit_kernel(int N, int dg,
     const int nb = dg == 1 ? kBins1 : kBins2;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) hloc[t] = 0u;
     __syncthreads();
-    for (int i = blockIdx.x; i < N - 1; i += gridDim.x) {
+    for (int i = cta; i < N - 1; i += ctas) {
         const float* row = d2 + (size_t)i * N;
         for (int j = i + 1 + threadIdx.x; j < N; j += blockDim.x) {
             const unsigned bits = __float_as_uint(row[j]);
@@ -178,7 +196,7 @@ __global__ void __launch_bounds__(256) median_digit_kernel(int N, int dg,
     unsigned* out = hist + (dg == 1 ? kBins0 : kBins0 + kBins1);
     for (int t = threadIdx.x; t < nb; t += blockDim.x)
         if (hloc[t]) atomicAdd(&out[t], hloc[t]);
-    if (last_block(counter, gridDim.x)) {
+    if (last_block(counter, (unsigned)ctas)) {
         if (dg == 1) {
             unsigned b1n, r1;
             find_bin<kBins1 / 256>(out, __ldcg(sel + 1), b1n, r1);
@@ -195,6 +213,27 @@ __global__ void __launch_bounds__(256) median_digit_kernel(int N, int dg,
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256) median_digit_kernel(int N, int dg,
+                                                           const float* __restrict__ d2,
+                                                           unsigned* __restrict__ hist,
+                                                           unsigned* __restrict__ sel,
+                                                           unsigned* __restrict__ counter,
+                                                           float* __restrict__ h_dev,
+                                                           float* __restrict__ h_out) {
+    median_digit_body(N, dg, d2, hist, sel, counter, h_dev, h_out, blockIdx.x, gridDim.x);
+}
+
+// Batched: work item (instance, CTA index) of the instance's med_ctas CTAs.
+__global__ void __launch_bounds__(256) median_digit_batch_kernel(const SvgdInst* __restrict__ inst,
+                                                                 const int2* __restrict__ items,
+                                                                 const int* __restrict__ active,
+                                                                 int dg) {
+    const int2 it = items[blockIdx.x];
+    const SvgdInst& g = inst[it.x];
+    if (!active[g.gid] || g.N < 2) return;
+    median_digit_body(g.N, dg, g.d2, g.hist, g.sel, g.counter + dg, g.h, nullptr, it.y, g.med_ctas);
 }
 
 // ---- TMA bulk copies and mbarriers (inline PTX) -----------------------------
@@ -246,21 +285,20 @@ __host__ __device__ constexpr int phi_stage_floats(int D, int DP) {
     return ((kTJ * D + 32 * DP) + 3) / 4 * 4;   // per array, 16-byte multiple
 }
 template <int DP>
-__global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ theta,
-                                                      const float* __restrict__ grad, int N, int D,
-                                                      const float* __restrict__ d2,
-                                                      const float* __restrict__ h_dev,
-                                                      float* __restrict__ part, int j_chunk,
-                                                      int* err) {
+__device__ __forceinline__ void phi_body(const float* __restrict__ theta,
+                                         const float* __restrict__ grad, int N, int D,
+                                         const float* __restrict__ d2,
+                                         const float* __restrict__ h_dev, float* __restrict__ part,
+                                         int j_chunk, int* err, int rblock, int share) {
     extern __shared__ __align__(128) float sm[];
     const int sf = phi_stage_floats(D, DP);
     // stage s: theta tile at sm + 2*s*sf, grad tile right after it
     float4* Ks = reinterpret_cast<float4*>(sm + 4 * sf);             // kW x kTJ
     uint64_t* bar = reinterpret_cast<uint64_t*>(Ks + kW * kTJ);       // 2 stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ib = (blockIdx.x * kW + warp) * kR;
+    const int ib = (rblock * kW + warp) * kR;
     // this CTA's share of the sum over j: rows [jb, je) of theta and grad
-    const int jb = blockIdx.y * j_chunk, je = min(N, jb + j_chunk);
+    const int jb = share * j_chunk, je = min(N, jb + j_chunk);
     const int ntiles = (je - jb + kTJ - 1) / kTJ;
     const float inv_h = 1.f / __ldcg(h_dev);
 
@@ -359,7 +397,7 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
     }
     // partial phi of this j-share; the Adam kernel sums the shares in order
     const float inv_n = 1.f / (float)N, two_h = 2.f * inv_h;
-    float* out = part + (size_t)blockIdx.y * N * D;
+    float* out = part + (size_t)share * N * D;
 #pragma unroll
     for (int r = 0; r < kR; ++r)
 #pragma unroll
@@ -368,6 +406,28 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
             if (ib + r < N && d < D)
                 out[(size_t)(ib + r) * D + d] = (ag[r][q] + two_h * ar[r][q]) * inv_n;
         }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ theta,
+                                                      const float* __restrict__ grad, int N, int D,
+                                                      const float* __restrict__ d2,
+                                                      const float* __restrict__ h_dev,
+                                                      float* __restrict__ part, int j_chunk,
+                                                      int* err) {
+    phi_body<DP>(theta, grad, N, D, d2, h_dev, part, j_chunk, err, blockIdx.x, blockIdx.y);
+}
+
+// Batched: work item (instance, row block, j-share); DP covers the batch's largest D.
+template <int DP>
+__global__ void __launch_bounds__(kW * 32) phi_batch_kernel(const SvgdInst* __restrict__ inst,
+                                                            const int4* __restrict__ items,
+                                                            const int* __restrict__ active,
+                                                            int* err) {
+    const int4 it = items[blockIdx.x];
+    const SvgdInst& g = inst[it.x];
+    if (!active[g.gid]) return;
+    phi_body<DP>(g.theta, g.grad, g.N, g.D, g.d2, g.h, g.part, g.j_chunk, err, it.y, it.z);
 }
 
 // Adam (Kingma & Ba 2015) with gradient -phi, phi the in-order sum of the
@@ -390,6 +450,39 @@ __global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__
     v[t] = vt;
     theta[t] = th;
     if (!isfinite(th) || !isfinite(g)) atomicOr(flag, 1);
+}
+
+// Batched Adam over the concatenated particles of all instances: element t
+// belongs to the last instance whose first element is <= t; its phi is the
+// in-order sum of that instance's shares.  step is read on the device.
+__global__ void adam_batch_kernel(float* __restrict__ theta, float* __restrict__ m,
+                                  float* __restrict__ v, long long n, const SvgdInst* __restrict__ inst,
+                                  int n_inst, const int* __restrict__ active,
+                                  const int* __restrict__ step_dev, const float2* __restrict__ bc,
+                                  float lr, int* flag) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&inst[mid].elem0) <= t) lo = mid; else hi = mid - 1;
+    }
+    const SvgdInst& g = inst[lo];
+    const long long loc = t - g.elem0, ne = (long long)g.N * g.D;
+    if (loc >= ne || !active[g.gid]) return;
+    const float* part = g.part;
+    float phi = part[loc];
+    for (int q = 1; q < g.shares; ++q) phi += part[(size_t)q * ne + loc];
+    const float2 b12 = bc[*step_dev + 1];
+    const float bc1 = b12.x, bc2 = b12.y;
+    const float gr = -phi;
+    const float mt = 0.9f * m[t] + 0.1f * gr;
+    const float vt = 0.999f * v[t] + 0.001f * gr * gr;
+    const float th = theta[t] - lr * (mt / bc1) / (sqrtf(vt / bc2) + 1e-8f);
+    m[t] = mt;
+    v[t] = vt;
+    theta[t] = th;
+    if (!isfinite(th) || !isfinite(gr)) atomicOr(flag, 1);
 }
 
 __global__ void init_theta_kernel(float* theta, int n, uint64_t key) {
@@ -475,7 +568,7 @@ cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch&
                             cudaStream_t st) {
     const int nt = (N + kTile - 1) / kTile;
     const size_t smem = 2 * kTile * (D + 1) * sizeof(float);
-    if (smem > 48 * 1024) {
+    if (smem + kPairwiseStatic > 48 * 1024) {   // static + dynamic above the default limit
         cudaError_t e = cudaFuncSetAttribute(pairwise_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -526,6 +619,68 @@ cudaError_t launch_adam(float* theta, const float* part, int shares, float* phi_
     const float bc2 = 1.f - powf(0.999f, (float)step);
     adam_kernel<<<(n + 255) / 256, 256, 0, st>>>(theta, part, shares, phi_out, m, v, n, lr, bc1,
                                                  bc2, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairwise_batch(const SvgdInst* inst, const int4* items, int n_items, int max_D,
+                                  const int* active, cudaStream_t st) {
+    const size_t smem = 2 * kTile * (max_D + 1) * sizeof(float);
+    if (smem + kPairwiseStatic > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(pairwise_batch_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    pairwise_batch_kernel<<<n_items, 256, smem, st>>>(inst, items, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_median_digit_batch(const SvgdInst* inst, const int2* items, int n_items,
+                                      const int* active, int digit, cudaStream_t st) {
+    median_digit_batch_kernel<<<n_items, 256, 0, st>>>(inst, items, active, digit);
+    return cudaGetLastError();
+}
+
+void phi_batch_plan(int N, int* shares, int* j_chunk) {
+    const int row_blocks = (N + kW * kR - 1) / (kW * kR);
+    int want = (4 * 152 + row_blocks - 1) / row_blocks;
+    want = want < 1 ? 1 : (want > kMaxShares ? kMaxShares : want);
+    *j_chunk = ((N + want - 1) / want + kTJ - 1) / kTJ * kTJ;
+    *shares = (N + *j_chunk - 1) / *j_chunk;
+}
+int phi_rows_per_block() { return kW * kR; }
+
+template <int DP>
+cudaError_t phi_batch_launch(const SvgdInst* inst, const int4* items, int n_items, int max_D,
+                             const int* active, int* err, cudaStream_t st) {
+    const size_t smem = (size_t)4 * phi_stage_floats(max_D, DP) * sizeof(float) +
+                        (size_t)kW * kTJ * sizeof(float4) + 2 * sizeof(uint64_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(phi_batch_kernel<DP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    phi_batch_kernel<DP><<<n_items, kW * 32, smem, st>>>(inst, items, active, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_batch(const SvgdInst* inst, const int4* items, int n_items, int max_D,
+                             const int* active, int* err, cudaStream_t st) {
+    switch ((max_D + 31) / 32) {
+        case 1: return phi_batch_launch<1>(inst, items, n_items, max_D, active, err, st);
+        case 2: return phi_batch_launch<2>(inst, items, n_items, max_D, active, err, st);
+        case 3: return phi_batch_launch<3>(inst, items, n_items, max_D, active, err, st);
+        case 4: return phi_batch_launch<4>(inst, items, n_items, max_D, active, err, st);
+        case 5: case 6: return phi_batch_launch<6>(inst, items, n_items, max_D, active, err, st);
+        case 7: case 8: case 9: return phi_batch_launch<9>(inst, items, n_items, max_D, active, err, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adam_batch(float* theta, float* m, float* v, long long n, const SvgdInst* inst,
+                              int n_inst, const int* active, const int* step_dev, const float2* bc,
+                              float lr, int* flag, cudaStream_t st) {
+    adam_batch_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, m, v, n, inst, n_inst, active,
+                                                                   step_dev, bc, lr, flag);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,12 @@ class stamp_problem_desc(ctypes.Structure):
         return cls(**{n: p[n] for n, _ in cls._fields_})
 
 
+class stamp_instance_desc(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int), ("H", ctypes.c_int), ("N", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("init", ctypes.c_float * 12),
+                ("goal", ctypes.c_float * 12)]
+
+
 _vp, _i, _ull, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float
 _sigs = {
     "stamp_problem_create": [ctypes.POINTER(stamp_problem_desc), _vp, _vp, _i, _vp,
@@ -79,6 +85,13 @@ _sigs = {
     "stamp_surrogate_dims": [_vp, _vp, _vp],
     "stamp_solve_surrogate": [_vp, _vp, _i, _i, _i, _i, _i, _ull, _f, _vp, _vp, _i, _vp, _vp],
     "stamp_set_target": [_vp, _f, _i],
+    "stamp_batch_create": [ctypes.POINTER(stamp_problem_desc), _vp, _i, _vp, ctypes.POINTER(_vp)],
+    "stamp_batch_set_config": [_vp, _i, _i, _i, _i],
+    "stamp_batch_get_config": [_vp, _i, _vp, _vp, _vp],
+    "stamp_batch_autotune": [_vp, _i],
+    "stamp_batch_solve": [_vp, _i, _f, _f, _i, _i],
+    "stamp_batch_results": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "stamp_batch_read_theta": [_vp, _i, _vp],
     "stamp_solve_info": [_vp, _vp, _vp],
 }
 for _name, _args in _sigs.items():
@@ -88,6 +101,8 @@ _lib.stamp_mlp_destroy.argtypes = [_vp]
 _lib.stamp_mlp_destroy.restype = None
 _lib.stamp_mlp_param_count.argtypes = [_i, _i]
 _lib.stamp_mlp_param_count.restype = ctypes.c_size_t
+_lib.stamp_batch_destroy.argtypes = [_vp]
+_lib.stamp_batch_destroy.restype = None
 _lib.stamp_surrogate_last_kept.argtypes = [_vp]
 _lib.stamp_surrogate_last_kept.restype = ctypes.c_int
 _lib.stamp_surrogate_destroy.argtypes = [_vp]
@@ -414,3 +429,70 @@ class MLP:
 
     def sync(self):
         _check(_lib.stamp_mlp_sync(self.handle))
+
+
+class Batch:
+    """Many planning instances solved together (stamp_batch_*).
+
+    instances: dicts with n_blocks, H, N, seed, init (n_blocks x 3), goal
+    (n_blocks x 3); physics: a parameter dict (its n_blocks/H are ignored)."""
+
+    def __init__(self, physics: dict, instances, cuda_stream: int | None = None):
+        arr = (stamp_instance_desc * len(instances))()
+        for d, inst in zip(arr, instances):
+            d.n_blocks, d.H, d.N, d.seed = inst["n_blocks"], inst["H"], inst["N"], inst["seed"]
+            init = np.zeros(12, dtype=np.float32)
+            goal = np.zeros(12, dtype=np.float32)
+            init[:3 * inst["n_blocks"]] = np.asarray(inst["init"], dtype=np.float32).ravel()
+            goal[:3 * inst["n_blocks"]] = np.asarray(inst["goal"], dtype=np.float32).ravel()
+            d.init[:] = init.tolist()
+            d.goal[:] = goal.tolist()
+        desc = stamp_problem_desc.from_params(dict(physics, n_blocks=1, H=1, ckpt_every=1))
+        out = _vp()
+        _check(_lib.stamp_batch_create(ctypes.byref(desc), ctypes.cast(arr, _vp), len(instances),
+                                       cuda_stream, ctypes.byref(out)))
+        self.handle = out.value
+        self.instances = [dict(i) for i in instances]
+        self.n = len(instances)
+
+    def close(self):
+        if self.handle:
+            _lib.stamp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_config(self, n_blocks, lanes, cta, ckpt_every):
+        _check(_lib.stamp_batch_set_config(self.handle, n_blocks, lanes, cta, ckpt_every))
+
+    def get_config(self, n_blocks):
+        l, c, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.stamp_batch_get_config(self.handle, n_blocks, ctypes.byref(l), ctypes.byref(c),
+                                           ctypes.byref(k)))
+        return l.value, c.value, k.value
+
+    def autotune(self, reps=2):
+        _check(_lib.stamp_batch_autotune(self.handle, reps))
+
+    def solve(self, iters, lr, target_cost=0.0, check_every=0, use_graph=True):
+        _check(_lib.stamp_batch_solve(self.handle, iters, lr, target_cost, check_every,
+                                      int(use_graph)))
+
+    def results(self) -> dict:
+        it = np.zeros(self.n, dtype=np.int32)
+        best = np.zeros(self.n, dtype=np.float32)
+        tts = np.zeros(self.n, dtype=np.float64)
+        top3 = np.zeros(3 * self.n, dtype=np.int32)
+        units, secs = ctypes.c_longlong(), ctypes.c_double()
+        _check(_lib.stamp_batch_results(self.handle, it.ctypes.data, best.ctypes.data,
+                                        tts.ctypes.data, top3.ctypes.data, ctypes.byref(units),
+                                        ctypes.byref(secs)))
+        return {"iterations": it, "best_cost": best, "seconds_to_target": tts,
+                "top3": top3.reshape(self.n, 3), "units": units.value, "seconds": secs.value}
+
+    def read_theta(self, instance, out):
+        _check(_lib.stamp_batch_read_theta(self.handle, instance, _f32(out, "theta_out")))

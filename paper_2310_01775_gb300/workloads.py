@@ -122,3 +122,20 @@ def mlp_init(sizes, seed: int):
         k = 1.0 / math.sqrt(i)
         out.append((rng.uniform(-k, k, size=(o, i)), rng.uniform(-k, k, size=o)))
     return out
+
+
+def batch_instances(n: int = 256, seed: int = 0, T: int = 100) -> list[dict]:
+    """Seeded uneven instances for batched serving: blocks uniform in 1..4,
+    horizon uniform in 2..8, particles log-uniform in [64, 1024] (rounded
+    down), scenes from `scene`; each instance has its own solve seed."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA7C4]))
+    out = []
+    for g in range(n):
+        nb = int(rng.integers(1, 5))
+        H = int(rng.integers(2, 9))
+        N = int(math.exp(rng.uniform(math.log(64), math.log(1024))))
+        p = dict(PHYSICS, n_blocks=nb, H=H, T=T)
+        init, goal = scene(p, 7919 * seed + g)
+        out.append({"n_blocks": nb, "H": H, "N": N, "seed": 100003 * seed + g,
+                    "init": init, "goal": goal})
+    return out

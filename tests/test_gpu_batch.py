@@ -1,0 +1,136 @@
+"""Batched serving (stamp_batch_*) on the GPU, through the C ABI.
+
+The batch runs the same kernels as a single problem, with per-instance
+constants and buffers, so every instance must come out bit for bit as the
+same instance solved alone by stamp_solve with the same lanes and checkpoint
+interval: particles, hard costs and top-3.  The single-problem path is itself
+parity-tested against the FP64 oracle.  Graph replay must equal direct
+launches; early stop must freeze exactly the instances that met the target.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2310_01775_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# (blocks, horizon, particles): every block count, ragged particle counts
+SHAPES = [(1, 2, 37), (2, 3, 64), (3, 2, 100), (4, 2, 45), (1, 4, 200), (3, 3, 33)]
+CONFIG = {1: (4, 64, 25), 2: (8, 64, 5), 3: (16, 128, 25), 4: (8, 128, 1)}   # lanes, cta, C
+
+
+def _S():
+    from paper_2310_01775_gb300 import stamp as S
+    return S
+
+
+def _instances(T=50):
+    out = []
+    for g, (nb, H, N) in enumerate(SHAPES):
+        p = dict(W.PHYSICS, n_blocks=nb, H=H, T=T)
+        init, goal = W.scene(p, 40 + g)
+        out.append({"n_blocks": nb, "H": H, "N": N, "seed": 1000 + g, "init": init, "goal": goal})
+    return out
+
+
+def _batch(insts, T=50):
+    S = _S()
+    b = S.Batch(dict(W.PHYSICS, T=T), insts, torch.cuda.current_stream().cuda_stream)
+    for nb, (l, c, k) in CONFIG.items():
+        b.set_config(nb, l, c, k)
+    return b
+
+
+def test_batch_equals_individual_solves_bitwise():
+    S = _S()
+    T, iters, lr = 50, 12, 1e-2
+    insts = _instances(T)
+    b = _batch(insts, T)
+    b.solve(iters, lr, use_graph=True)
+    res = b.results()
+    for g, d in enumerate(insts):
+        l, c, k = CONFIG[d["n_blocks"]]
+        P = dict(W.PHYSICS, n_blocks=d["n_blocks"], H=d["H"], T=T, ckpt_every=k)
+        prob = S.Problem(P, d["init"], d["goal"], d["N"], torch.cuda.current_stream().cuda_stream)
+        prob.set_lanes(l, l)
+        th = torch.empty(d["N"], prob.D, device="cuda")
+        cost = torch.empty(d["N"], device="cuda")
+        top = np.zeros(3, dtype=np.int32)
+        prob.solve(d["N"], iters, 0, d["seed"], lr, None, th, cost, 3, top, None)
+        prob.sync()
+        got = torch.empty_like(th)
+        b.read_theta(g, got)
+        assert torch.equal(got, th), (g, float((got - th).abs().max()))
+        assert res["best_cost"][g] == float(cost.min()), g
+        assert list(res["top3"][g]) == list(top), g
+        assert res["iterations"][g] == iters
+        prob.close()
+    units = sum(d["N"] * d["H"] * T for d in insts) * iters
+    assert res["units"] == units
+    b.close()
+
+
+def test_graph_replay_equals_direct_launches():
+    T = 50
+    insts = _instances(T)
+    a, b = _batch(insts, T), _batch(insts, T)
+    a.solve(9, 1e-2, target_cost=0.0, check_every=4, use_graph=True)
+    b.solve(9, 1e-2, target_cost=0.0, check_every=4, use_graph=False)
+    ra, rb = a.results(), b.results()
+    for g, d in enumerate(insts):
+        D = d["H"] * (4 * d["n_blocks"] + 2)
+        x = torch.empty(d["N"], D, device="cuda")
+        y = torch.empty_like(x)
+        a.read_theta(g, x)
+        b.read_theta(g, y)
+        assert torch.equal(x, y), g
+    assert np.array_equal(ra["best_cost"], rb["best_cost"])
+    a.close()
+    b.close()
+
+
+def test_early_stop_freezes_instances_at_the_target():
+    T = 50
+    insts = _instances(T)
+    b = _batch(insts, T)
+    # a target between the instances' costs after the first check
+    b.solve(4, 1e-2, target_cost=0.0, check_every=4)
+    first = b.results()["best_cost"]
+    target = float(np.median(first))
+    b.solve(12, 1e-2, target_cost=target, check_every=4)
+    res = b.results()
+    stopped = res["seconds_to_target"] >= 0
+    assert stopped.any() and not stopped.all(), (first, target)
+    assert (res["iterations"][stopped] <= 12).all()
+    assert (res["iterations"][~stopped] == 12).all()
+    # a stopped instance's particles are those of the check that stopped it
+    g = int(np.nonzero(stopped & (res["iterations"] == 4))[0][0])
+    d = insts[g]
+    D = d["H"] * (4 * d["n_blocks"] + 2)
+    frozen = torch.empty(d["N"], D, device="cuda")
+    b.read_theta(g, frozen)
+    ref = _batch(insts, T)
+    ref.solve(4, 1e-2)
+    want = torch.empty_like(frozen)
+    ref.read_theta(g, want)
+    assert torch.equal(frozen, want)
+    ref.close()
+    b.close()
+
+
+def test_autotune_picks_supported_configs_and_solves():
+    from paper_2310_01775_gb300 import stamp as S
+    insts = _instances(50)
+    b = S.Batch(dict(W.PHYSICS, T=50), insts, torch.cuda.current_stream().cuda_stream)
+    b.autotune(1)
+    for nb in range(1, 5):
+        l, c, k = b.get_config(nb)
+        assert l in (1, 2, 4, 8, 16, 32) and c in (64, 128) and k in (1, 5, 25)
+    b.solve(5, 1e-2)
+    assert np.isfinite(b.results()["best_cost"]).all()
+    with pytest.raises(S.StampError):
+        b.set_config(1, 3, 64, 25)          # unsupported lane count
+    with pytest.raises(S.StampError):
+        b.set_config(2, 8, 64, 7)           # does not divide T
+    b.close()

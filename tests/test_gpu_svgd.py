@@ -16,9 +16,9 @@ from paper_2310_01775_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def make_problem(N, name="pusher1_h2"):
+def make_problem(N, name="pusher1_h2", **over):
     from paper_2310_01775_gb300 import stamp as S
-    P = W.params(name)
+    P = W.params(name, **over)
     init, goal = W.scene(P, 0)
     return S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream), P
 
@@ -33,11 +33,13 @@ def term_scale(theta, g, h):
     return out
 
 
-@pytest.mark.parametrize("N,name", [(1, "pusher1_h2"), (2, "pusher1_h2"), (32, "pusher1_h2"),
-                                    (37, "pusher1_h4"), (1024, "pusher1_h4"),
-                                    (2048, "pusher3_h6")])
-def test_svgd_step_parity(N, name):
-    prob, P = make_problem(N, name)
+@pytest.mark.parametrize("N,name,over", [(1, "pusher1_h2", {}), (2, "pusher1_h2", {}),
+                                         (32, "pusher1_h2", {}), (37, "pusher1_h4", {}),
+                                         (1024, "pusher1_h4", {}), (2048, "pusher3_h6", {}),
+                                         # the largest particle dimension: 4 blocks, H = 8 (D = 144)
+                                         (300, "pusher3_h6", {"n_blocks": 4, "H": 8})])
+def test_svgd_step_parity(N, name, over):
+    prob, P = make_problem(N, name, **over)
     D = prob.D
     dev = "cuda"
     theta = W.random_theta(N, D, 3 + N)
