@@ -34,7 +34,8 @@ METRIC = "particle rollout+adjoint steps/s"
 UNIT = "particle-substeps/s"
 # Algorithmic FLOPs per unit (one particle, one substep), counted over the
 # oracle's own operations (oracle/flops.py): forward, reverse sweep.
-FLOPS_PER_UNIT = {1: (447.2, 863.2), 2: None, 3: (6293.5, 12860.9)}
+FLOPS_PER_UNIT = {1: (447.2, 863.2), 2: (2544.4, 5005.0), 3: (6293.5, 12860.9),
+                  4: (11694.7, 24711.2)}
 SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes, 1 FMA = 2 FLOP
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture (profiles/rollout_pusher1_h4.md), valid while the kernel source is
@@ -212,6 +213,13 @@ def batched_serving(stream, n=256, iters=500, target=1e-3, check_every=10):
     r = b.results()
     stopped = r["seconds_to_target"] >= 0
     tts = np.sort(r["seconds_to_target"][stopped])
+    # FP32-ALU roofline of the whole batch: the oracle's FLOPs per unit of each
+    # block count (forward + reverse) over the units each instance ran
+    flops = sum(int(r["iterations"][g]) * d["N"] * d["H"] * 100 * sum(FLOPS_PER_UNIT[d["n_blocks"]])
+                for g, d in enumerate(insts))
+    mhz, _, src = peaks()
+    peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    ach = flops / r["seconds"] / 1e12
     done = np.where(stopped, r["seconds_to_target"], r["seconds"])
     b.close()
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
@@ -224,7 +232,10 @@ def batched_serving(stream, n=256, iters=500, target=1e-3, check_every=10):
                                    "over": "instances that reached the target"},
             "time_to_stop_s": {"p50": pct(done, 50), "p99": pct(done, 99),
                                "over": "all instances (unreached: the solve's end)"},
-            "median_iterations": float(np.median(r["iterations"]))}
+            "median_iterations": float(np.median(r["iterations"])),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "over": "the whole solve (all kernels, checks included)",
+                         "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz ({src})"}}
 
 
 def workload_config(args, P):

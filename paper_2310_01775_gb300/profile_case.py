@@ -2,6 +2,7 @@
 
     python -m paper_2310_01775_gb300.profile_case pusher1_h4 20
     python -m paper_2310_01775_gb300.profile_case surrogate 20
+    python -m paper_2310_01775_gb300.profile_case batch 20      # or batch64: first 64 instances
 
 Builds the workload's problem (seed 0 scene), runs `iters` SVGD iterations
 plus the hard evaluation and top-3 on the current CUDA device, and prints the
@@ -43,9 +44,26 @@ def surrogate_case(iters: int) -> float:
     return float(cost.min())
 
 
+def batch_case(iters: int, n: int = 256) -> float:
+    """The first n of the 256 seeded serving instances (uniform goals), with the
+    launch configuration the autotuner picks on GB300, `iters` iterations
+    launched one by one."""
+    insts = W.batch_instances(256)[:n]
+    b = S.Batch(dict(W.PHYSICS, T=100), insts, torch.cuda.current_stream().cuda_stream)
+    for nb, cfg in {1: (2, 64, 1), 2: (4, 128, 1), 3: (8, 128, 1), 4: (8, 128, 1)}.items():
+        if any(d["n_blocks"] == nb for d in insts):
+            b.set_config(nb, *cfg)
+    b.solve(iters, 1e-2, use_graph=False)
+    best = float(b.results()["best_cost"].min())
+    b.close()
+    return best
+
+
 def main(name: str = "pusher1_h4", iters: int = 2) -> float:
     if name == "surrogate":
         return surrogate_case(iters)
+    if name.startswith("batch"):
+        return batch_case(iters, int(name[5:] or 256))
     P = W.params(name)
     init, goal = W.scene(P, 0)
     N = P["N"]
