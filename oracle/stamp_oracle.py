@@ -433,21 +433,35 @@ def median_bandwidth(theta):
     return h if h >= 1e-12 else 1.0
 
 
-def stein_direction(theta, grad_logp, h, chunk=128):
-    """phi_i = (1/N) sum_j [ k_ji grad log p(theta_j) + grad_{theta_j} k_ji ]
+def stein_direction(theta, grad_logp, h, chunk=128, weights=None):
+    """phi_i = sum_j (w_j / w) [ k_ji grad log p(theta_j) + grad_{theta_j} k_ji ]
     with k(a, b) = exp(-|a - b|^2 / h), so grad_{theta_j} k_ji =
-    (2/h) (theta_i - theta_j) k_ji  [Eq. svgd, terms (A) and (B)]."""
+    (2/h) (theta_i - theta_j) k_ji  [Eq. svgd, terms (A) and (B); Eq. dsvgd
+    with its weights w_j, w = sum_j w_j].  weights=None: w_j = 1, so the
+    factor is 1/N."""
     th = np.asarray(theta, dtype=np.float64)
     g = np.asarray(grad_logp, dtype=np.float64)
     n = th.shape[0]
+    wn = (np.full(n, 1.0 / n) if weights is None
+          else np.asarray(weights, dtype=np.float64) / np.sum(weights))
     phi = np.empty_like(th)
     for i0 in range(0, n, chunk):
         diff = th[i0:i0 + chunk, None, :] - th[None, :, :]        # theta_i - theta_j
-        k = np.exp(-(diff * diff).sum(-1) / h)                   # (c, N)
+        k = np.exp(-(diff * diff).sum(-1) / h) * wn[None, :]     # (c, N), weighted
         attract = k @ g
         repulse = (2.0 / h) * (k[:, :, None] * diff).sum(1)
-        phi[i0:i0 + chunk] = (attract + repulse) / n
+        phi[i0:i0 + chunk] = attract + repulse
     return phi
+
+
+def dsvgd_weights(cost_relaxed, cost_hard):
+    """Importance weights of Eq. dsvgd, w_j = p~*(Gamma~(theta_j)) / p*(Gamma(theta_j)),
+    with p* proportional to exp(-C) [Eq. neglog_likelihood]: the relaxed plan's
+    cost against the hard plan's (the same Gumbel draws), w_j = exp(C_j - C~_j).
+    Returned divided by their sum (the update uses w_j / w only)."""
+    d = np.asarray(cost_hard, dtype=np.float64) - np.asarray(cost_relaxed, dtype=np.float64)
+    w = np.exp(d - d.max())
+    return w / w.sum()
 
 
 ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8

@@ -96,3 +96,54 @@ def test_topk_distinct_plans():
     assert O.topk_plans(costs, codes, 5) == [5, 4, 3, -1, -1]
     # equal costs: the lower index wins
     assert O.topk_plans(np.array([1.0, 1.0]), np.array([[0], [1]]), 1) == [0]
+
+
+# ---- Eq. dsvgd importance weights ---------------------------------------------
+
+
+def test_weighted_stein_direction_against_autograd_loop():
+    """sum_j (w_j/w) [k_ji g_j + grad_{theta_j} k_ji], written out pair by pair
+    with autograd for the kernel gradient."""
+    rng = np.random.default_rng(5)
+    n, d, h = 7, 3, 0.9
+    th, g = rng.standard_normal((n, d)), rng.standard_normal((n, d))
+    w = rng.uniform(0.1, 3.0, n)
+    phi = O.stein_direction(th, g, h, weights=w)
+    T = torch.tensor(th)
+    ref = np.zeros((n, d))
+    for i in range(n):
+        for j in range(n):
+            tj = T[j].clone().requires_grad_(True)
+            kji = torch.exp(-((tj - T[i]) ** 2).sum() / h)
+            (gk,) = torch.autograd.grad(kji, tj)
+            ref[i] += w[j] / w.sum() * (float(kji.detach()) * g[j] + gk.numpy())
+    assert np.allclose(phi, ref, rtol=1e-12, atol=1e-13)
+
+
+def test_equal_weights_are_plain_svgd_and_one_weight_is_one_particle():
+    rng = np.random.default_rng(6)
+    n, d, h = 8, 4, 1.3
+    th, g = rng.standard_normal((n, d)), rng.standard_normal((n, d))
+    assert np.allclose(O.stein_direction(th, g, h, weights=np.full(n, 2.5)),
+                       O.stein_direction(th, g, h), rtol=1e-13, atol=1e-14)
+    # all weight on particle 3: phi_i = k_i3 g_3 + (2/h) k_i3 (theta_i - theta_3)
+    w = np.zeros(n)
+    w[3] = 1.0
+    k = np.exp(-((th - th[3]) ** 2).sum(1) / h)
+    want = k[:, None] * g[3] + (2 / h) * k[:, None] * (th - th[3])
+    assert np.allclose(O.stein_direction(th, g, h, weights=w), want, rtol=1e-12, atol=1e-14)
+
+
+def test_dsvgd_weights_definition_and_shift_invariance():
+    """w_j proportional to exp(C_j - C~_j) (hard against relaxed cost), summing
+    to one; adding one constant to every cost leaves them unchanged; a
+    particle whose relaxed plan is as good as its hard plan weighs e^{-1}
+    of one whose relaxed cost is lower by one."""
+    cr = np.array([1.0, 2.0, 0.5, 3.0])
+    ch = np.array([1.0, 3.0, 0.5, 3.0])
+    w = O.dsvgd_weights(cr, ch)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(w / w[0], [1.0, math.e, 1.0, 1.0])
+    assert np.allclose(O.dsvgd_weights(cr + 7.0, ch + 7.0), w)
+    big = O.dsvgd_weights(np.zeros(3), np.array([0.0, 800.0, 0.0]))   # no overflow
+    assert np.isfinite(big).all() and abs(big[1] - 1.0) < 1e-12
