@@ -264,6 +264,8 @@ def main():
                     help="skip the surrogate-assisted vs plain SVGD comparison")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256-instance batched serving run")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the SVGD / SVGD+SGD / DSVGD cost-evolution comparison")
     args = ap.parse_args()
 
     from paper_2310_01775_gb300 import workloads as W
@@ -373,6 +375,10 @@ def main():
         sur = surrogate_vs_plain(stream.cuda_stream)
     if world == 1 and not args.no_batched:
         bat = batched_serving(stream.cuda_stream)
+    var = None
+    if world == 1 and not args.no_variants:
+        from paper_2310_01775_gb300 import variants as V
+        var = V.cost_evolution("pusher1_h4", (0, 1, 2, 3, 4), stream=stream.cuda_stream)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -380,7 +386,7 @@ def main():
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": int(sum(n for _, n in kt.values())),
             "kernels_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]},
-            "surrogate_vs_plain": sur, "batched_serving": bat}
+            "surrogate_vs_plain": sur, "batched_serving": bat, "solver_variants": var}
     print(json.dumps(line), flush=True)
     prob.close()
     if world > 1:

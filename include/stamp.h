@@ -356,6 +356,23 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
                                    int surrogate_iters, int sim_iters, int sgd_iters,
                                    unsigned long long seed, float lr, float* theta_out,
                                    float* cost_out, int k, int* topk_particle, float* stats_out);
+/* Importance weights of Eq. dsvgd, w_j = p~*(Gamma~(theta_j)) / p*(Gamma(theta_j))
+ * = exp(C_j - C~_j) with C~_j the relaxed and C_j the hard cost of particle j
+ * under the same Gumbel draws; the Stein direction becomes
+ * phi_i = sum_j (w_j / w) [k_ji grad log rho_j + grad_{theta_j} k_ji],
+ * w = sum_j w_j (unit weights give the 1/N of stamp_svgd_step).  A particle
+ * whose cost difference is not finite weighs 0.
+ * stamp_svgd_step_weighted: one such step from the two cost arrays (device
+ * N each); other arguments as stamp_svgd_step (SVGD phase only).
+ * stamp_set_dsvgd(prob, 1): stamp_solve and stamp_solve_surrogate weight
+ * every SVGD iteration on the simulator this way (one extra hard rollout of
+ * the iteration's draws per iteration); 0 (default): unit weights. */
+stamp_status stamp_svgd_step_weighted(stamp_problem* prob, float* theta, const float* grad_logp,
+                                      const float* cost_relaxed, const float* cost_hard, int N,
+                                      float* adam_m, float* adam_v, int step, float lr,
+                                      float* h_out, float* phi_out);
+stamp_status stamp_set_dsvgd(stamp_problem* prob, int enable);
+
 /* Early stop for stamp_solve and stamp_solve_surrogate: every check_every
  * iterations (0: never) the particles are rolled out hard on the simulator
  * without noise and the solve ends when the lowest cost is below

@@ -67,6 +67,8 @@ struct stamp_problem {
     // early stop of the solves, and what the last solve did
     float target = 0.f;
     int check_every = 0;
+    bool dsvgd = false;          // Eq. dsvgd importance weights in the solves' SVGD iterations
+    float *cost_hard = nullptr, *wn = nullptr;
     int iters_run = 0;
     float best_hard = 0.f;
     // kernel timing
@@ -164,7 +166,8 @@ stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
 }
 
 stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, float* m, float* v,
-                  int step, float lr, int sgd_phase, float* h_out, float* phi_out) {
+                  int step, float lr, int sgd_phase, float* h_out, float* phi_out,
+                  const float* wn = nullptr) {
     const int D = p->sc.D;
     const float* part = grad;   // SGD phase: phi = grad log rho, one share
     int shares = 1;
@@ -184,7 +187,7 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
         }
         STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
             return stamp::launch_phi(theta, grad, N, D, s, p->phi, stamp::kMaxShares, &shares,
-                                     p->stream);
+                                     p->stream, wn);
         }));
         part = p->phi;
     } else if (h_out) {
@@ -273,8 +276,16 @@ stamp_status run_solve(stamp_problem* p, const Phases& ph, int N, unsigned long 
             STAMP_TRY(fwd(p, th, N, seed, (int)it, 0, p->cost, nullptr, sw));
             STAMP_TRY(adj(p, th, N, p->grad));
         }
-        STAMP_TRY(svgd(p, th, p->grad, N, p->m, p->v, (int)it + 1, lr,
-                       it >= (long long)ph.sur + ph.svgd ? 1 : 0, nullptr, nullptr));
+        const bool sgd = it >= (long long)ph.sur + ph.svgd;
+        const float* wn = nullptr;
+        if (p->dsvgd && !sgd && it >= ph.sur) {
+            // Eq. dsvgd: the hard plan of the same Gumbel draws against the relaxed one
+            STAMP_TRY(fwd(p, th, N, seed, (int)it, 1, p->cost_hard, nullptr, nullptr));
+            STAMP_CUDA(stamp::launch_dsvgd_weights(p->cost, p->cost_hard, N, p->wn, p->stream));
+            wn = p->wn;
+        }
+        STAMP_TRY(svgd(p, th, p->grad, N, p->m, p->v, (int)it + 1, lr, sgd ? 1 : 0, nullptr,
+                       nullptr, wn));
         if (p->check_every > 0 && (it + 1) % p->check_every == 0) {
             STAMP_TRY(hard_min(p, th, N, seed, p->cost, &p->best_hard));
             if (p->best_hard < p->target) {
@@ -455,6 +466,8 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         {(void**)&p->sel, 4 * sizeof(unsigned)},
         {(void**)&p->counter, 3 * sizeof(unsigned)},
         {(void**)&p->stop, sizeof(unsigned)},
+        {(void**)&p->cost_hard, n * sizeof(float)},
+        {(void**)&p->wn, n * sizeof(float)},
     };
     size_t total = 0;
     for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
@@ -588,6 +601,34 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
         return fail(STAMP_EINVAL, "negative iteration count");
     Phases ph{s, n_candidates, surrogate_iters, sim_iters, sgd_iters};
     return run_solve(p, ph, N, seed, lr, nullptr, theta_out, cost_out, k, topk_particle, stats_out);
+}
+
+stamp_status stamp_set_dsvgd(stamp_problem* p, int enable) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    p->dsvgd = enable != 0;
+    return STAMP_OK;
+}
+
+stamp_status stamp_svgd_step_weighted(stamp_problem* p, float* theta, const float* grad_logp,
+                                      const float* cost_relaxed, const float* cost_hard, int N,
+                                      float* adam_m, float* adam_v, int step, float lr,
+                                      float* h_out, float* phi_out) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_n(p, N));
+    STAMP_TRY(check_dev(theta, "theta"));
+    STAMP_TRY(check_dev(grad_logp, "grad_logp"));
+    STAMP_TRY(check_dev(cost_relaxed, "cost_relaxed"));
+    STAMP_TRY(check_dev(cost_hard, "cost_hard"));
+    STAMP_TRY(check_dev(adam_m, "adam_m"));
+    STAMP_TRY(check_dev(adam_v, "adam_v"));
+    STAMP_TRY(check_dev(h_out, "h_out", true));
+    STAMP_TRY(check_dev(phi_out, "phi_out", true));
+    if (step < 1) return fail(STAMP_EINVAL, "step must be >= 1");
+    if ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(grad_logp)) & 15u)
+        return fail(STAMP_EINVAL, "theta and grad_logp must be 16-byte aligned");
+    if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
+    STAMP_CUDA(stamp::launch_dsvgd_weights(cost_relaxed, cost_hard, N, p->wn, p->stream));
+    return svgd(p, theta, grad_logp, N, adam_m, adam_v, step, lr, 0, h_out, phi_out, p->wn);
 }
 
 stamp_status stamp_set_target(stamp_problem* p, float target_cost, int check_every) {

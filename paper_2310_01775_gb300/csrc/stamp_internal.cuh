@@ -122,8 +122,13 @@ cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h
                                 cudaStream_t st);
 // Writes `*shares` partial Stein directions (N x D each, consecutive) to part;
 // at most max_shares.
+// wn: normalised importance weights of Eq. dsvgd (device N), or NULL: 1/N.
 cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
-                       float* part, int max_shares, int* shares, cudaStream_t st);
+                       float* part, int max_shares, int* shares, cudaStream_t st,
+                       const float* wn = nullptr);
+// Normalised Eq. dsvgd weights from the relaxed and hard costs (device N each).
+cudaError_t launch_dsvgd_weights(const float* c_relaxed, const float* c_hard, int N, float* wn,
+                                 cudaStream_t st);
 // Adam on -phi, phi = sum of the `shares` partials (stride n_elems); writes
 // phi to phi_out when given.
 cudaError_t launch_adam(float* theta, const float* part, int shares, float* phi_out, float* m,

@@ -289,7 +289,8 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
                                          const float* __restrict__ grad, int N, int D,
                                          const float* __restrict__ d2,
                                          const float* __restrict__ h_dev, float* __restrict__ part,
-                                         int j_chunk, int* err, int rblock, int share) {
+                                         int j_chunk, int* err, int rblock, int share,
+                                         const float* __restrict__ wn) {
     extern __shared__ __align__(128) float sm[];
     const int sf = phi_stage_floats(D, DP);
     // stage s: theta tile at sm + 2*s*sf, grad tile right after it
@@ -347,6 +348,11 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
             float kv[kR];
 #pragma unroll
             for (int r = 0; r < kR; ++r) kv[r] = (ib + r < N && lane < nj) ? expf(-dv[r] * inv_h) : 0.f;
+            if (wn) {   // Eq. dsvgd: k_ij scaled by w_j / w
+                const float wj = lane < nj ? wn[j0 + lane] : 0.f;
+#pragma unroll
+                for (int r = 0; r < kR; ++r) kv[r] *= wj;
+            }
             Ks[warp * kTJ + lane] = make_float4(kv[0], kv[1], kv[2], kv[3]);
         }
         if (t + 1 < ntiles) {   // next tile's distances, consumed one iteration later
@@ -396,7 +402,7 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
         }
     }
     // partial phi of this j-share; the Adam kernel sums the shares in order
-    const float inv_n = 1.f / (float)N, two_h = 2.f * inv_h;
+    const float inv_n = wn ? 1.f : 1.f / (float)N, two_h = 2.f * inv_h;
     float* out = part + (size_t)share * N * D;
 #pragma unroll
     for (int r = 0; r < kR; ++r)
@@ -414,8 +420,8 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
                                                       const float* __restrict__ d2,
                                                       const float* __restrict__ h_dev,
                                                       float* __restrict__ part, int j_chunk,
-                                                      int* err) {
-    phi_body<DP>(theta, grad, N, D, d2, h_dev, part, j_chunk, err, blockIdx.x, blockIdx.y);
+                                                      int* err, const float* __restrict__ wn) {
+    phi_body<DP>(theta, grad, N, D, d2, h_dev, part, j_chunk, err, blockIdx.x, blockIdx.y, wn);
 }
 
 // Batched: work item (instance, row block, j-share); DP covers the batch's largest D.
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(kW * 32) phi_batch_kernel(const SvgdInst* __re
     const int4 it = items[blockIdx.x];
     const SvgdInst& g = inst[it.x];
     if (!active[g.gid]) return;
-    phi_body<DP>(g.theta, g.grad, g.N, g.D, g.d2, g.h, g.part, g.j_chunk, err, it.y, it.z);
+    phi_body<DP>(g.theta, g.grad, g.N, g.D, g.d2, g.h, g.part, g.j_chunk, err, it.y, it.z, nullptr);
 }
 
 // Adam (Kingma & Ba 2015) with gradient -phi, phi the in-order sum of the
@@ -483,6 +489,43 @@ __global__ void adam_batch_kernel(float* __restrict__ theta, float* __restrict__
     v[t] = vt;
     theta[t] = th;
     if (!isfinite(th) || !isfinite(gr)) atomicOr(flag, 1);
+}
+
+// Eq. dsvgd weights, normalised: w_j = exp(C_j - C~_j - max) / sum, C the hard
+// and C~ the relaxed cost of particle j; a non-finite difference weighs 0.
+// One CTA; fixed per-thread strides and a fixed tree: deterministic.
+__global__ void __launch_bounds__(1024) dsvgd_weights_kernel(const float* __restrict__ c_relaxed,
+                                                            const float* __restrict__ c_hard, int N,
+                                                            float* __restrict__ wn) {
+    __shared__ float red[1024];
+    float mx = -INFINITY;
+    for (int j = threadIdx.x; j < N; j += 1024) {
+        const float d = c_hard[j] - c_relaxed[j];
+        if (isfinite(d)) mx = fmaxf(mx, d);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    mx = red[0];
+    __syncthreads();
+    float sum = 0.f;
+    for (int j = threadIdx.x; j < N; j += 1024) {
+        const float d = c_hard[j] - c_relaxed[j];
+        const float e = isfinite(d) ? expf(d - mx) : 0.f;
+        wn[j] = e;
+        sum += e;
+    }
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const float inv = red[0] > 0.f ? 1.f / red[0] : 0.f;
+    for (int j = threadIdx.x; j < N; j += 1024) wn[j] *= inv;
 }
 
 __global__ void init_theta_kernel(float* theta, int n, uint64_t key) {
@@ -548,7 +591,7 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ th
 template <int DP>
 cudaError_t phi_launch(const float* theta, const float* grad, int N, int D, const float* d2,
                        const float* h_dev, float* part, int shares, int j_chunk, int* err,
-                       cudaStream_t st) {
+                       const float* wn, cudaStream_t st) {
     const size_t smem = (size_t)4 * phi_stage_floats(D, DP) * sizeof(float) +
                         (size_t)kW * kTJ * sizeof(float4) + 2 * sizeof(uint64_t);
     if (smem > 48 * 1024) {
@@ -558,7 +601,7 @@ cudaError_t phi_launch(const float* theta, const float* grad, int N, int D, cons
     }
     const int rows = kW * kR;
     phi_kernel<DP><<<dim3((N + rows - 1) / rows, shares), kW * 32, smem, st>>>(
-        theta, grad, N, D, d2, h_dev, part, j_chunk, err);
+        theta, grad, N, D, d2, h_dev, part, j_chunk, err, wn);
     return cudaGetLastError();
 }
 
@@ -588,7 +631,7 @@ cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h
 }
 
 cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
-                       float* part, int max_shares, int* shares, cudaStream_t st) {
+                       float* part, int max_shares, int* shares, cudaStream_t st, const float* wn) {
     // TMA bulk copies need 16-byte aligned sources
     if ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(grad)) & 15u)
         return cudaErrorMisalignedAddress;
@@ -601,14 +644,14 @@ cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, cons
     *shares = (N + j_chunk - 1) / j_chunk;
     const int dp = (D + 31) / 32;
     switch (dp) {
-        case 1: return phi_launch<1>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
-        case 2: return phi_launch<2>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
-        case 3: return phi_launch<3>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
-        case 4: return phi_launch<4>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+        case 1: return phi_launch<1>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
+        case 2: return phi_launch<2>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
+        case 3: return phi_launch<3>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
+        case 4: return phi_launch<4>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
         case 5: case 6:
-            return phi_launch<6>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+            return phi_launch<6>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
         case 7: case 8: case 9:
-            return phi_launch<9>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, st);
+            return phi_launch<9>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -681,6 +724,12 @@ cudaError_t launch_adam_batch(float* theta, float* m, float* v, long long n, con
                               float lr, int* flag, cudaStream_t st) {
     adam_batch_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, m, v, n, inst, n_inst, active,
                                                                    step_dev, bc, lr, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dsvgd_weights(const float* c_relaxed, const float* c_hard, int N, float* wn,
+                                 cudaStream_t st) {
+    dsvgd_weights_kernel<<<1, 1024, 0, st>>>(c_relaxed, c_hard, N, wn);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,8 @@ _sigs = {
     "stamp_surrogate_dims": [_vp, _vp, _vp],
     "stamp_solve_surrogate": [_vp, _vp, _i, _i, _i, _i, _i, _ull, _f, _vp, _vp, _i, _vp, _vp],
     "stamp_set_target": [_vp, _f, _i],
+    "stamp_set_dsvgd": [_vp, _i],
+    "stamp_svgd_step_weighted": [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _i, _f, _vp, _vp],
     "stamp_batch_create": [ctypes.POINTER(stamp_problem_desc), _vp, _i, _vp, ctypes.POINTER(_vp)],
     "stamp_batch_set_config": [_vp, _i, _i, _i, _i],
     "stamp_batch_get_config": [_vp, _i, _vp, _vp, _vp],
@@ -305,6 +307,20 @@ class Problem:
                                           surrogate_iters, sim_iters, sgd_iters, seed, lr,
                                           _f32(theta_out, "theta_out"), _f32(cost_out, "cost_out"),
                                           k, _ptr(topk_particle), _f32(stats_out, "stats_out")))
+
+    def svgd_step_weighted(self, theta, grad_logp, cost_relaxed, cost_hard, N, adam_m, adam_v,
+                           step, lr, h_out=None, phi_out=None):
+        """Stein step with the importance weights of Eq. dsvgd from the two costs."""
+        _check(_lib.stamp_svgd_step_weighted(self.handle, _f32(theta, "theta"),
+                                             _f32(grad_logp, "grad_logp"),
+                                             _f32(cost_relaxed, "cost_relaxed"),
+                                             _f32(cost_hard, "cost_hard"), N,
+                                             _f32(adam_m, "adam_m"), _f32(adam_v, "adam_v"), step,
+                                             lr, _f32(h_out, "h_out"), _f32(phi_out, "phi_out")))
+
+    def set_dsvgd(self, enable):
+        """Eq. dsvgd importance weights in the solves' SVGD iterations."""
+        _check(_lib.stamp_set_dsvgd(self.handle, int(enable)))
 
     def set_target(self, target_cost, check_every):
         """Early stop of the solves on the lowest hard, noise-free simulator cost."""

@@ -117,3 +117,72 @@ def test_nonfinite_particles_are_reported():
     assert e.value.status == S.STAMP_ENONFINITE
     prob.sync()            # the flag is cleared once reported
     prob.close()
+
+
+# ---- Eq. dsvgd importance weights -----------------------------------------------
+
+
+def weighted_term_scale(theta, g, h, wn):
+    th = theta.astype(np.float64)
+    out = np.zeros_like(th)
+    for i0 in range(0, len(th), 128):
+        diff = th[i0:i0 + 128, None, :] - th[None, :, :]
+        k = np.exp(-(diff ** 2).sum(-1) / h) * wn[None, :]
+        out[i0:i0 + 128] = k @ np.abs(g) + (2 / h) * (k[:, :, None] * np.abs(diff)).sum(1)
+    return out
+
+
+@pytest.mark.parametrize("N,name,over", [(37, "pusher1_h4", {}), (1024, "pusher1_h4", {}),
+                                         (300, "pusher3_h6", {"n_blocks": 4, "H": 8})])
+def test_weighted_svgd_step_parity(N, name, over):
+    prob, P = make_problem(N, name, **over)
+    D = prob.D
+    theta = W.random_theta(N, D, 13 + N)
+    g = W.random_normal((N, D), 14 + N)
+    cr = np.abs(W.random_normal(N, 15 + N)) + 0.5
+    ch = cr + np.abs(W.random_normal(N, 16 + N, 0.7))   # hard plans cost more
+    m0 = W.random_normal((N, D), 17 + N, 0.1)
+    v0 = np.abs(W.random_normal((N, D), 18 + N, 0.1)) + 1e-3
+    t = lambda x: torch.tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+    th_d, g_d, m_d, v_d = t(theta), t(g), t(m0), t(v0)
+    h_d, phi_d = torch.zeros(1, device="cuda"), torch.zeros(N, D, device="cuda")
+    prob.svgd_step_weighted(th_d, g_d, t(cr), t(ch), N, m_d, v_d, 4, 1e-2, h_d, phi_d)
+    prob.sync()
+    prob.close()
+    h_ref = O.median_bandwidth(theta)
+    wn = O.dsvgd_weights(cr.astype(np.float32), ch.astype(np.float32))
+    phi_ref = O.stein_direction(theta, g, h_ref, weights=wn)
+    A = weighted_term_scale(theta, g, h_ref, wn)
+    err = np.abs(phi_d.cpu().numpy() - phi_ref)
+    assert (err <= 1e-5 * A + 1e-9).all(), float((err / (A + 1e-12)).max())
+    th_ref, _, _ = O.adam_update(theta.astype(np.float64), m0.astype(np.float64),
+                                 v0.astype(np.float64), -phi_ref, 4, 1e-2)
+    assert np.abs(th_d.cpu().numpy() - th_ref).max() <= 1e-5
+
+
+def test_solve_with_dsvgd_weights_follows_the_oracle():
+    """Three iterations of stamp_solve with the weights on, against the oracle
+    doing the same steps (relaxed rollout and gradient, hard rollout of the
+    same Gumbel draws, weights, weighted Stein direction, Adam), under the
+    softer contact model whose trajectories are well conditioned."""
+    from paper_2310_01775_gb300 import stamp as S
+    P = W.params("pusher1_h2", k_contact=1e3, c_contact=10.0)
+    init, goal = W.scene(P, 3)
+    N, seed, iters = 32, 21, 3
+    prob = S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream)
+    prob.set_dsvgd(1)
+    th = torch.zeros(N, prob.D, device="cuda")
+    prob.solve(N, iters, 0, seed, P["lr"], None, th, None)
+    prob.close()
+    M, _, D = O.dims(P)
+    theta = O.init_theta(seed, N, D).astype(np.float32).astype(np.float64)
+    m, v = np.zeros_like(theta), np.zeros_like(theta)
+    for it in range(iters):
+        gum = O.gumbel_noise(seed, it, N, P["H"], M)
+        cr, glp = O.rollout_grad(theta, P, init, goal, gum)
+        ch, _ = O.rollout(theta, P, init, goal, gum, hard=True)
+        phi = O.stein_direction(theta, glp, O.median_bandwidth(theta),
+                                weights=O.dsvgd_weights(cr, ch))
+        theta, m, v = O.adam_update(theta, m, v, -phi, it + 1, P["lr"])
+    got = th.cpu().numpy()
+    assert np.abs(got - theta).max() <= 1e-4 * np.abs(theta).max(), float(np.abs(got - theta).max())
