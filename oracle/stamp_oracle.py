@@ -454,6 +454,62 @@ def stein_direction(theta, grad_logp, h, chunk=128, weights=None):
     return phi
 
 
+def structured_parts(theta, P):
+    """Per-action components of the structured kernel: the continuous push
+    parameters c_k = (u_k, v_k) (N, H, 2) and the choice probabilities
+    s_k = softmax(a_k) (N, H, M)."""
+    M, Pn, _ = dims(P)
+    th = torch.as_tensor(np.asarray(theta), dtype=torch.float64).reshape(-1, P["H"], Pn)
+    return th[..., M:], torch.softmax(th[..., :M], dim=-1)
+
+
+def structured_bandwidths(theta, P):
+    """(h_c, h_z): the median heuristic of each component on its per-action
+    mean squared distance, (1/H) sum_k |x_ik - x_jk|^2, lower median over
+    i < j, divided by ln(N+1): the plain bandwidth of the concatenated
+    component divided by H (so 1/H in the plain rule's degenerate cases)."""
+    c, z = structured_parts(theta, P)
+    n = c.shape[0]
+    return tuple(median_bandwidth(x.reshape(n, -1).numpy()) / P["H"] for x in (c, z))
+
+
+def structured_kernel(theta_a, theta_b, P, h_c, h_z):
+    """App. D.3's additive kernel restated for this parameterisation:
+    K(a, b) = (1/2H) sum_k [exp(-|c_k(a) - c_k(b)|^2 / h_c)
+                            + exp(-|softmax(a_k) - softmax(b_k)|^2 / h_z)]
+    (torch, differentiable; K(a, a) = 1)."""
+    ca, za = structured_parts_t(theta_a, P)
+    cb, zb = structured_parts_t(theta_b, P)
+    kc = torch.exp(-((ca - cb) ** 2).sum(-1) / h_c)
+    kz = torch.exp(-((za - zb) ** 2).sum(-1) / h_z)
+    return (kc + kz).sum(-1) / (2 * P["H"])
+
+
+def structured_parts_t(theta, P):
+    M, Pn, _ = dims(P)
+    th = theta.reshape(*theta.shape[:-1], P["H"], Pn)
+    return th[..., M:], torch.softmax(th[..., :M], dim=-1)
+
+
+def stein_direction_structured(theta, grad_logp, P, weights=None):
+    """phi_i = sum_j (w_j / w) [K(theta_j, theta_i) grad log p(theta_j)
+    + grad_{theta_j} K(theta_j, theta_i)] with the structured kernel [Eq. svgd /
+    Eq. dsvgd, kernel of App. D.3]; the kernel gradient by reverse mode."""
+    th = torch.as_tensor(np.asarray(theta), dtype=torch.float64)
+    g = torch.as_tensor(np.asarray(grad_logp), dtype=torch.float64)
+    n = th.shape[0]
+    h_c, h_z = structured_bandwidths(th.numpy(), P)
+    wn = (torch.full((n,), 1.0 / n, dtype=torch.float64) if weights is None
+          else torch.as_tensor(np.asarray(weights, dtype=np.float64) / np.sum(weights)))
+    tj = th.clone().requires_grad_(True)
+    phi = torch.zeros_like(th)
+    for i in range(n):
+        k = structured_kernel(tj, th[i].expand_as(th), P, h_c, h_z)   # K(theta_j, theta_i), (n,)
+        (gk,) = torch.autograd.grad((k * wn).sum(), tj)
+        phi[i] = ((k.detach() * wn)[:, None] * g).sum(0) + gk.sum(0)
+    return phi.numpy()
+
+
 def dsvgd_weights(cost_relaxed, cost_hard):
     """Importance weights of Eq. dsvgd, w_j = p~*(Gamma~(theta_j)) / p*(Gamma(theta_j)),
     with p* proportional to exp(-C) [Eq. neglog_likelihood]: the relaxed plan's

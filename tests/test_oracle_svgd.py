@@ -147,3 +147,84 @@ def test_dsvgd_weights_definition_and_shift_invariance():
     assert np.allclose(O.dsvgd_weights(cr + 7.0, ch + 7.0), w)
     big = O.dsvgd_weights(np.zeros(3), np.array([0.0, 800.0, 0.0]))   # no overflow
     assert np.isfinite(big).all() and abs(big[1] - 1.0) < 1e-12
+
+
+# ---- the structured kernel (App. D.3, restated for offset/distance and choice parameters)
+
+
+def _struct_case(n=6, nb=2, H=2, seed=0):
+    from paper_2310_01775_gb300 import workloads as W
+    P = W.params("pusher1_h2", n_blocks=nb, H=H)
+    M, _, D = O.dims(P)
+    th = np.random.default_rng(seed).standard_normal((n, D))
+    return P, M, D, th
+
+
+def test_structured_kernel_is_one_on_the_diagonal_symmetric_and_psd():
+    P, M, D, th = _struct_case(n=12)
+    h_c, h_z = O.structured_bandwidths(th, P)
+    T = torch.tensor(th)
+    G = np.array([[float(O.structured_kernel(T[i], T[j], P, h_c, h_z)) for j in range(12)]
+                  for i in range(12)])
+    assert np.allclose(np.diag(G), 1.0) and np.allclose(G, G.T)
+    assert np.linalg.eigvalsh(G).min() > -1e-12
+
+
+def test_structured_bandwidths_are_per_action_mean_medians():
+    P, M, D, th = _struct_case(n=9, nb=1, H=3)
+    c, z = O.structured_parts(th, P)
+    for x, h in zip((c, z), O.structured_bandwidths(th, P)):
+        f = x.reshape(9, -1).numpy()
+        vals = np.sort(pdist(f, "sqeuclidean")) / P["H"]
+        assert abs(h - vals[(vals.size - 1) // 2] / math.log(10)) < 1e-12
+
+
+def test_structured_kernel_gradient_against_central_differences():
+    P, M, D, th = _struct_case(n=5, seed=3)
+    h_c, h_z = O.structured_bandwidths(th, P)
+    a, b = torch.tensor(th[1]), torch.tensor(th[3])
+    ar = a.clone().requires_grad_(True)
+    (g,) = torch.autograd.grad(O.structured_kernel(ar, b, P, h_c, h_z), ar)
+    eps = 1e-6
+    for d in range(D):
+        e = torch.zeros(D, dtype=torch.float64)
+        e[d] = eps
+        fd = (O.structured_kernel(a + e, b, P, h_c, h_z) - O.structured_kernel(a - e, b, P, h_c, h_z)) / (2 * eps)
+        assert abs(float(fd) - float(g[d])) < 1e-8
+
+
+def test_structured_repulsion_ignores_a_common_logit_shift():
+    """softmax(a_k) is unchanged by adding one constant to all of action k's
+    logits, so the kernel is, and its gradient has no component along that
+    direction: each action's logit entries of the repulsive term sum to zero
+    (with grad log p = 0 the Stein direction is the repulsion alone)."""
+    P, M, D, th = _struct_case(n=7, nb=2, H=2, seed=4)
+    phi = O.stein_direction_structured(th, np.zeros_like(th), P)
+    Pn = M + 2
+    for k in range(P["H"]):
+        assert np.abs(phi[:, k * Pn:k * Pn + M].sum(1)).max() < 1e-13
+    shifted = th.copy()
+    shifted[:, :M] += 0.7
+    assert np.allclose(O.stein_direction_structured(shifted, np.zeros_like(th), P), phi, atol=1e-13)
+
+
+def test_structured_direction_written_out_for_one_action():
+    """H = 1, one block: the attraction is K_ij g_j, the repulsion's offset and
+    distance entries (2/h_c)(c_i - c_j) e^c_ij / (2H) and its logit entries
+    (2/h_z) e^z_ij J(a_j)^T (s_i - s_j) / (2H), J the softmax Jacobian."""
+    P, M, D, th = _struct_case(n=5, nb=1, H=1, seed=8)
+    g = np.random.default_rng(9).standard_normal(th.shape)
+    h_c, h_z = O.structured_bandwidths(th, P)
+    a, c = th[:, :M], th[:, M:]
+    s = np.exp(a - a.max(1, keepdims=True))
+    s /= s.sum(1, keepdims=True)
+    want = np.zeros_like(th)
+    for i in range(5):
+        for j in range(5):
+            ec = math.exp(-((c[i] - c[j]) ** 2).sum() / h_c)
+            ez = math.exp(-((s[i] - s[j]) ** 2).sum() / h_z)
+            kij = (ec + ez) / 2
+            J = np.diag(s[j]) - np.outer(s[j], s[j])
+            rep = np.concatenate([(2 / h_z) * ez * J.T @ (s[i] - s[j]), (2 / h_c) * ec * (c[i] - c[j])]) / 2
+            want[i] += (kij * g[j] + rep) / 5
+    assert np.allclose(O.stein_direction_structured(th, g, P), want, rtol=1e-11, atol=1e-13)
