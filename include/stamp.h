@@ -373,6 +373,21 @@ stamp_status stamp_svgd_step_weighted(stamp_problem* prob, float* theta, const f
                                       float* h_out, float* phi_out);
 stamp_status stamp_set_dsvgd(stamp_problem* prob, int enable);
 
+/* Kernel of the Stein direction (stamp_svgd_step, stamp_svgd_step_weighted
+ * and the solves' SVGD iterations):
+ *   0 (default): k(a, b) = exp(-|a - b|^2 / h) on the whole plan (Eq. svgd);
+ *   1: App. D.3's additive kernel restated for these plans,
+ *      K(a, b) = (1/2H) sum_k [exp(-|c_k(a) - c_k(b)|^2 / h_c)
+ *                              + exp(-|softmax(a_k) - softmax(b_k)|^2 / h_z)],
+ *      c_k = the offset and distance parameters (u_k, v_k) of action k,
+ *      a_k its logits; h_c, h_z the median heuristic of each component on
+ *      its per-action mean squared distance (the paper's kernel acts on DMP
+ *      goal poses, with a von Mises term for goal yaws that has no
+ *      counterpart here).  h_out then receives h_c.
+ * Kind 1 allocates its scratch on first use (N^2 floats for the second
+ * median, and the per-action components). */
+stamp_status stamp_set_svgd_kernel(stamp_problem* prob, int kind);
+
 /* Early stop for stamp_solve and stamp_solve_surrogate: every check_every
  * iterations (0: never) the particles are rolled out hard on the simulator
  * without noise and the solve ends when the lowest cost is below

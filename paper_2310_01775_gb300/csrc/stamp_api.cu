@@ -69,6 +69,11 @@ struct stamp_problem {
     int check_every = 0;
     bool dsvgd = false;          // Eq. dsvgd importance weights in the solves' SVGD iterations
     float *cost_hard = nullptr, *wn = nullptr;
+    // structured kernel (App. D.3 restated): components and a second median scratch
+    int kernel_kind = 0;
+    char* sk_arena = nullptr;
+    float *sk_C = nullptr, *sk_S = nullptr, *sk_d2 = nullptr, *sk_h = nullptr;
+    unsigned *sk_hist = nullptr, *sk_sel = nullptr, *sk_counter = nullptr;
     int iters_run = 0;
     float best_hard = 0.f;
     // kernel timing
@@ -171,7 +176,33 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
     const int D = p->sc.D;
     const float* part = grad;   // SGD phase: phi = grad log rho, one share
     int shares = 1;
-    if (!sgd_phase) {
+    if (!sgd_phase && p->kernel_kind == 1) {
+        // structured kernel: bandwidths of the offset/distance and choice components
+        const int H = p->sc.H, M = p->sc.M;
+        STAMP_CUDA(stamp::launch_struct_prep(theta, N, H, M, p->sk_C, p->sk_S, p->stream));
+        stamp::SvgdScratch a{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
+        stamp::SvgdScratch b{p->sk_d2, p->sk_hist, p->sk_sel, p->sk_counter, p->sk_h, p->flag};
+        const stamp::SvgdScratch* ss[2] = {&a, &b};
+        const float* comp[2] = {p->sk_C, p->sk_S};
+        const int width[2] = {2 * H, M * H};
+        for (int q = 0; q < 2; ++q) {
+            STAMP_CUDA(cudaMemsetAsync(ss[q]->hist, 0, (2048 + 2048 + 1024) * sizeof(unsigned), p->stream));
+            STAMP_TRY(timed(p, STAMP_K_PAIRWISE, [&] {
+                return stamp::launch_pairwise(comp[q], N, width[q], *ss[q], p->stream);
+            }));
+            if (N >= 2)
+                for (int dg = 1; dg <= 2; ++dg)
+                    STAMP_TRY(timed(p, STAMP_K_MEDIAN, [&] {
+                        return stamp::launch_median_digit(N, dg, *ss[q], nullptr, p->stream);
+                    }));
+        }
+        if (h_out) STAMP_CUDA(stamp::launch_scale_scalar(p->h, 1.f / (float)H, h_out, p->stream));
+        STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
+            return stamp::launch_struct_phi(theta, grad, p->sk_C, p->sk_S, N, H, M, p->h, p->sk_h, wn,
+                                            p->phi, p->stream);
+        }));
+        part = p->phi;
+    } else if (!sgd_phase) {
         stamp::SvgdScratch s{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
         STAMP_CUDA(cudaMemsetAsync(p->hist, 0, (2048 + 2048 + 1024) * sizeof(unsigned), p->stream));
         STAMP_TRY(timed(p, STAMP_K_PAIRWISE,
@@ -500,6 +531,7 @@ void stamp_problem_destroy(stamp_problem* p) {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    cudaFree(p->sk_arena);
     cudaFree(p->arena);
     delete p;
 }
@@ -601,6 +633,33 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
         return fail(STAMP_EINVAL, "negative iteration count");
     Phases ph{s, n_candidates, surrogate_iters, sim_iters, sgd_iters};
     return run_solve(p, ph, N, seed, lr, nullptr, theta_out, cost_out, k, topk_particle, stats_out);
+}
+
+stamp_status stamp_set_svgd_kernel(stamp_problem* p, int kind) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    if (kind != 0 && kind != 1) return fail(STAMP_EINVAL, "kernel kind must be 0 (RBF) or 1 (structured)");
+    if (kind == 1 && !p->sk_arena) {
+        const size_t n = (size_t)p->max_n, H = p->sc.H, M = p->sc.M;
+        const size_t bytes[] = {n * 2 * H * 4, n * M * H * 4, n * n * 4, 4,
+                                (2048 + 2048 + 1024) * 4, 4 * 4, 3 * 4};
+        size_t total = 0;
+        for (size_t b : bytes) total += (b + 255) / 256 * 256;
+        if (cudaMalloc(&p->sk_arena, total) != cudaSuccess) {
+            cudaGetLastError();
+            p->sk_arena = nullptr;
+            return fail(STAMP_ENOMEM, "cudaMalloc of %zu bytes for the structured kernel failed", total);
+        }
+        void** dst[] = {(void**)&p->sk_C, (void**)&p->sk_S, (void**)&p->sk_d2, (void**)&p->sk_h,
+                        (void**)&p->sk_hist, (void**)&p->sk_sel, (void**)&p->sk_counter};
+        char* q = p->sk_arena;
+        for (size_t k = 0; k < sizeof bytes / sizeof bytes[0]; ++k) {
+            *dst[k] = q;
+            q += (bytes[k] + 255) / 256 * 256;
+        }
+        STAMP_CUDA(cudaMemset(p->sk_arena, 0, total));
+    }
+    p->kernel_kind = kind;
+    return STAMP_OK;
 }
 
 stamp_status stamp_set_dsvgd(stamp_problem* p, int enable) {

@@ -86,6 +86,7 @@ _sigs = {
     "stamp_solve_surrogate": [_vp, _vp, _i, _i, _i, _i, _i, _ull, _f, _vp, _vp, _i, _vp, _vp],
     "stamp_set_target": [_vp, _f, _i],
     "stamp_set_dsvgd": [_vp, _i],
+    "stamp_set_svgd_kernel": [_vp, _i],
     "stamp_svgd_step_weighted": [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _i, _f, _vp, _vp],
     "stamp_batch_create": [ctypes.POINTER(stamp_problem_desc), _vp, _i, _vp, ctypes.POINTER(_vp)],
     "stamp_batch_set_config": [_vp, _i, _i, _i, _i],
@@ -317,6 +318,11 @@ class Problem:
                                              _f32(cost_hard, "cost_hard"), N,
                                              _f32(adam_m, "adam_m"), _f32(adam_v, "adam_v"), step,
                                              lr, _f32(h_out, "h_out"), _f32(phi_out, "phi_out")))
+
+    def set_svgd_kernel(self, kind):
+        """0: RBF on the whole plan; 1: the structured kernel (per-action RBFs on
+        the push parameters and on softmax(a_k))."""
+        _check(_lib.stamp_set_svgd_kernel(self.handle, int(kind)))
 
     def set_dsvgd(self, enable):
         """Eq. dsvgd importance weights in the solves' SVGD iterations."""

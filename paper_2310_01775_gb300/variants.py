@@ -8,6 +8,9 @@ total iteration budget:
   * "svgd+sgd":    SVGD, then plain-gradient (SGD-phase) iterations;
   * "dsvgd":       SVGD with the importance weights of Eq. dsvgd;
   * "dsvgd+sgd":   the weighted SVGD, then SGD;
+  * "structured", "structured+sgd": SVGD with the structured kernel of
+    App. D.3 (restated: per-action RBFs on the push parameters and on the
+    choice probabilities), without and with the SGD refinement;
 and reports per variant the lowest relaxed cost at a few iterations (the
 cost-evolution curve), the final lowest hard cost and the wall time.
 """
@@ -21,8 +24,10 @@ import torch
 from . import stamp as S
 from . import workloads as W
 
-VARIANTS = {"svgd": (False, False), "svgd+sgd": (False, True), "dsvgd": (True, False),
-            "dsvgd+sgd": (True, True)}
+# name: (DSVGD weights, SGD refinement, structured kernel)
+VARIANTS = {"svgd": (False, False, 0), "svgd+sgd": (False, True, 0), "dsvgd": (True, False, 0),
+            "dsvgd+sgd": (True, True, 0), "structured": (False, False, 1),
+            "structured+sgd": (False, True, 1)}
 
 
 def cost_evolution(name: str, seeds, iters: int = 500, sgd_iters: int = 200,
@@ -30,12 +35,13 @@ def cost_evolution(name: str, seeds, iters: int = 500, sgd_iters: int = 200,
     P = W.params(name)
     N = P["N"]
     out = {}
-    for var, (weighted, refine) in VARIANTS.items():
+    for var, (weighted, refine, kind) in VARIANTS.items():
         curves, finals, secs = [], [], []
         for seed in seeds:
             init, goal = W.scene(P, seed)
             prob = S.Problem(P, init, goal, N, stream)
             prob.set_dsvgd(weighted)
+            prob.set_svgd_kernel(kind)
             th = torch.empty(N, prob.D, device="cuda")
             cost = torch.empty(N, device="cuda")
             stats = np.zeros(iters, dtype=np.float32)

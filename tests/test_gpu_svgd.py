@@ -186,3 +186,54 @@ def test_solve_with_dsvgd_weights_follows_the_oracle():
         theta, m, v = O.adam_update(theta, m, v, -phi, it + 1, P["lr"])
     got = th.cpu().numpy()
     assert np.abs(got - theta).max() <= 1e-4 * np.abs(theta).max(), float(np.abs(got - theta).max())
+
+
+# ---- structured kernel (App. D.3 restated) ----------------------------------------------
+
+
+@pytest.mark.parametrize("N,name,over,weighted", [(37, "pusher1_h4", {}, False),
+                                                  (300, "pusher3_h6", {}, False),
+                                                  (130, "pusher3_h6", {"n_blocks": 2, "H": 3}, True)])
+def test_structured_kernel_step_parity(N, name, over, weighted):
+    prob, P = make_problem(N, name, **over)
+    prob.set_svgd_kernel(1)
+    D = prob.D
+    theta = W.random_theta(N, D, 23 + N, scale=2.0)
+    g = W.random_normal((N, D), 24 + N)
+    m0 = np.zeros((N, D), dtype=np.float32)
+    v0 = np.zeros((N, D), dtype=np.float32)
+    t = lambda x: torch.tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+    th_d, g_d, m_d, v_d = t(theta), t(g), t(m0), t(v0)
+    h_d, phi_d = torch.zeros(1, device="cuda"), torch.zeros(N, D, device="cuda")
+    wn = None
+    if weighted:
+        cr = np.abs(W.random_normal(N, 25 + N)) + 0.5
+        ch = cr + np.abs(W.random_normal(N, 26 + N, 0.7))
+        prob.svgd_step_weighted(th_d, g_d, t(cr), t(ch), N, m_d, v_d, 1, 1e-2, h_d, phi_d)
+        wn = O.dsvgd_weights(cr.astype(np.float32), ch.astype(np.float32))
+    else:
+        prob.svgd_step(th_d, g_d, N, m_d, v_d, 1, 1e-2, 0, h_d, phi_d)
+    prob.sync()
+    prob.close()
+    h_c, _ = O.structured_bandwidths(theta.astype(np.float64), P)
+    assert abs(float(h_d) - h_c) <= 1e-5 * h_c
+    phi_ref = O.stein_direction_structured(theta.astype(np.float64), g.astype(np.float64), P, weights=wn)
+    err = np.abs(phi_d.cpu().numpy() - phi_ref).max()
+    assert err <= 1e-4 * np.abs(phi_ref).max(), err / np.abs(phi_ref).max()
+
+
+def test_solve_with_the_structured_kernel_runs_and_differs_from_rbf():
+    from paper_2310_01775_gb300 import stamp as S
+    P = W.params("pusher1_h2")
+    init, goal = W.scene(P, 4)
+    out = []
+    for kind in (0, 1):
+        prob = S.Problem(P, init, goal, 32, torch.cuda.current_stream().cuda_stream)
+        prob.set_svgd_kernel(kind)
+        th = torch.zeros(32, prob.D, device="cuda")
+        cost = torch.zeros(32, device="cuda")
+        prob.solve(32, 30, 5, 9, P["lr"], None, th, cost)
+        prob.close()
+        assert torch.isfinite(th).all() and torch.isfinite(cost).all()
+        out.append(th)
+    assert not torch.equal(out[0], out[1])
