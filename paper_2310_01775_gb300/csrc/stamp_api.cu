@@ -199,7 +199,7 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
         if (h_out) STAMP_CUDA(stamp::launch_scale_scalar(p->h, 1.f / (float)H, h_out, p->stream));
         STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
             return stamp::launch_struct_phi(theta, grad, p->sk_C, p->sk_S, N, H, M, p->h, p->sk_h, wn,
-                                            p->phi, p->stream);
+                                            p->phi, stamp::kMaxShares, &shares, p->stream);
         }));
         part = p->phi;
     } else if (!sgd_phase) {

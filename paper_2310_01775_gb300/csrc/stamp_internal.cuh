@@ -131,9 +131,11 @@ cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, cons
 // the raw bandwidths of C and S (h_plain, divided by H inside).
 cudaError_t launch_struct_prep(const float* theta, int N, int H, int M, float* C, float* S,
                                cudaStream_t st);
+// Writes `*shares` partial directions (N x D each, consecutive; at most max_shares).
 cudaError_t launch_struct_phi(const float* theta, const float* grad, const float* C, const float* S,
                               int N, int H, int M, const float* hc_dev, const float* hz_dev,
-                              const float* wn, float* phi, cudaStream_t st);
+                              const float* wn, float* phi, int max_shares, int* shares,
+                              cudaStream_t st);
 cudaError_t launch_scale_scalar(const float* src, float s, float* dst, cudaStream_t st);
 // Normalised Eq. dsvgd weights from the relaxed and hard costs (device N each).
 cudaError_t launch_dsvgd_weights(const float* c_relaxed, const float* c_hard, int N, float* wn,

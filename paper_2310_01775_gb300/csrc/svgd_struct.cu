@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kRows * 32)
 struct_phi_kernel(const float* __restrict__ theta, const float* __restrict__ grad,
                   const float* __restrict__ C, const float* __restrict__ S, int N, int H, int M,
                   const float* __restrict__ hc_dev, const float* __restrict__ hz_dev,
-                  const float* __restrict__ wn, float* __restrict__ phi) {
+                  const float* __restrict__ wn, float* __restrict__ phi, int j_chunk) {
     __shared__ float Ec[kRows][kTJ][kMaxHs + 1], Ez[kRows][kTJ][kMaxHs + 1], Q[kRows][kTJ][kMaxHs + 1];
     __shared__ float Ks[kRows][kTJ];
     const int P = M + 2, D = H * P;
@@ -68,8 +68,11 @@ struct_phi_kernel(const float* __restrict__ theta, const float* __restrict__ gra
         si[q] = (ok && d % P < M) ? S[(size_t)i * M * H + (d / P) * M + d % P] : 0.f;
         acc[q] = 0.f;
     }
-    for (int j0 = 0; j0 < N; j0 += kTJ) {
-        const int nj = min(kTJ, N - j0);
+    // this CTA's share of the sum over j; partial directions go to share blockIdx.y
+    const int jb = blockIdx.y * j_chunk, je = min(N, jb + j_chunk);
+    phi += (size_t)blockIdx.y * N * D;
+    for (int j0 = jb; j0 < je; j0 += kTJ) {
+        const int nj = min(kTJ, je - j0);
         // per (row, j, action): e^c, e^z and s_j.(s_i - s_j)
         for (int e = tid; e < kRows * kTJ * H; e += kRows * 32) {
             const int r = e / (kTJ * H), jj = (e / H) % kTJ, k = e % H;
@@ -153,16 +156,23 @@ cudaError_t launch_struct_prep(const float* theta, int N, int H, int M, float* C
 
 cudaError_t launch_struct_phi(const float* theta, const float* grad, const float* C, const float* S,
                               int N, int H, int M, const float* hc_dev, const float* hz_dev,
-                              const float* wn, float* phi, cudaStream_t st) {
+                              const float* wn, float* phi, int max_shares, int* shares,
+                              cudaStream_t st) {
     if (H > kMaxHs) return cudaErrorInvalidValue;
-    const int D = H * (M + 2), grid = (N + kRows - 1) / kRows;
+    const int D = H * (M + 2), rows = (N + kRows - 1) / kRows;
+    // split the sum over j so that about four CTAs per SM are in flight
+    int want = (4 * 152 + rows - 1) / rows;
+    want = want < 1 ? 1 : (want > max_shares ? max_shares : want);
+    const int j_chunk = ((N + want - 1) / want + kTJ - 1) / kTJ * kTJ;
+    *shares = (N + j_chunk - 1) / j_chunk;
+    const dim3 grid(rows, *shares);
     switch ((D + 31) / 32) {
-        case 1: struct_phi_kernel<1><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi); break;
-        case 2: struct_phi_kernel<2><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi); break;
-        case 3: struct_phi_kernel<3><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi); break;
-        case 4: struct_phi_kernel<4><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi); break;
-        case 5: case 6: struct_phi_kernel<6><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi); break;
-        case 7: case 8: case 9: struct_phi_kernel<9><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi); break;
+        case 1: struct_phi_kernel<1><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi, j_chunk); break;
+        case 2: struct_phi_kernel<2><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi, j_chunk); break;
+        case 3: struct_phi_kernel<3><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi, j_chunk); break;
+        case 4: struct_phi_kernel<4><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi, j_chunk); break;
+        case 5: case 6: struct_phi_kernel<6><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi, j_chunk); break;
+        case 7: case 8: case 9: struct_phi_kernel<9><<<grid, kRows * 32, 0, st>>>(theta, grad, C, S, N, H, M, hc_dev, hz_dev, wn, phi, j_chunk); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -3,6 +3,7 @@
     python -m paper_2310_01775_gb300.profile_case pusher1_h4 20
     python -m paper_2310_01775_gb300.profile_case surrogate 20
     python -m paper_2310_01775_gb300.profile_case batch 20      # or batch64: first 64 instances
+    python -m paper_2310_01775_gb300.profile_case structured 20  # or dsvgd: pusher1_h4 variants
 
 Builds the workload's problem (seed 0 scene), runs `iters` SVGD iterations
 plus the hard evaluation and top-3 on the current CUDA device, and prints the
@@ -59,7 +60,26 @@ def batch_case(iters: int, n: int = 256) -> float:
     return best
 
 
+def variant_case(name: str, iters: int) -> float:
+    """pusher1_h4 solve with the Stein-step variant `name`: "dsvgd" (importance
+    weights) or "structured" (the structured kernel)."""
+    P = W.params("pusher1_h4")
+    init, goal = W.scene(P, 0)
+    N = P["N"]
+    prob = S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream)
+    prob.set_dsvgd(name == "dsvgd")
+    prob.set_svgd_kernel(1 if name == "structured" else 0)
+    theta = torch.empty(N, prob.D, device="cuda")
+    cost = torch.empty(N, device="cuda")
+    prob.solve(N, iters, 0, 0, P["lr"], None, theta, cost)
+    torch.cuda.synchronize()
+    prob.close()
+    return float(cost.min())
+
+
 def main(name: str = "pusher1_h4", iters: int = 2) -> float:
+    if name in ("dsvgd", "structured"):
+        return variant_case(name, iters)
     if name == "surrogate":
         return surrogate_case(iters)
     if name.startswith("batch"):
