@@ -85,16 +85,6 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    return world, rank, local
-
-
 def cpu_oracle_sample(P, init, goal, seed, n_particles, iters=1):
     """Time the FP64 oracle on a bounded sample: n_particles of the workload,
     `iters` iterations of rollout + reverse sweep + Stein step."""
@@ -270,8 +260,8 @@ def main():
 
     from paper_2310_01775_gb300 import workloads as W
     P = W.params(args.workload, **({"ckpt_every": args.ckpt} if args.ckpt else {}))
-    world, rank, local = dist_setup() if args.impl == "ours" else (
-        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    from paper_2310_01775_gb300 import replicas as R
+    world, rank, local = R.init() if args.impl == "ours" else R.env()
     if args.impl == "reference":
         run_reference(args, P, world, rank)
         return
@@ -281,7 +271,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    seed = args.seed + 1000 * rank
+    seed = R.rank_seed(args.seed, rank)
     init, goal = W.scene(P, seed)
     N, H, T, iters = P["N"], P["H"], P["T"], P["svgd_iters"]
     prob = S.Problem(P, init, goal, N, stream.cuda_stream)
@@ -301,8 +291,7 @@ def main():
         step(s)
     # timed region: per-step CUDA events on the problem's stream, L2 flushed in between
     prob.set_profiling(True)
-    if world > 1:
-        torch.distributed.barrier()
+    R.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
     evs = []
@@ -318,12 +307,9 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in evs)
     kt = prob.kernel_times()
     prob.set_profiling(False)
-    t_max = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-    ms_max = float(t_max)
-    value = units * args.steps * world / (ms_max / 1e3)
+    ms_max = R.max_over_ranks(ms, device=dev)
+    R.barrier()
+    value = R.throughput(units * args.steps, world, ms_max)
 
     # end to end through the public call with host buffers (pinned)
     th_h = torch.empty(N, D, pin_memory=True)
@@ -340,8 +326,7 @@ def main():
 
     if rank != 0:
         prob.close()
-        if world > 1:
-            torch.distributed.destroy_process_group()
+        R.finish()
         return
 
     # roofline of the dominant kernel (FP32 ALU bound; FLOPs from the oracle count)
@@ -389,8 +374,7 @@ def main():
             "surrogate_vs_plain": sur, "batched_serving": bat, "solver_variants": var}
     print(json.dumps(line), flush=True)
     prob.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    R.finish()
 
 
 if __name__ == "__main__":
