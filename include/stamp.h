@@ -193,6 +193,13 @@ stamp_status stamp_set_profiling(stamp_problem* prob, int enable);
 /* ms_out, launches_out: host arrays of STAMP_NKERNELS (either may be NULL). */
 stamp_status stamp_get_kernel_times(stamp_problem* prob, double* ms_out, long long* launches_out);
 
+/* The solves compute each SVGD iteration's RBF bandwidth (pairwise
+ * distances and median, which depend on the particles only) on a second
+ * stream of the problem's own, concurrently with the iteration's rollouts,
+ * and the Stein direction waits for both (enable = 1, the default); 0: one
+ * after the other on the problem's stream.  Results are identical. */
+stamp_status stamp_set_overlap(stamp_problem* prob, int enable);
+
 /* Lanes per particle used by the rollout kernels (1,2,4,8,16,32; 0 = automatic). */
 stamp_status stamp_set_lanes(stamp_problem* prob, int fwd_lanes, int adj_lanes);
 

@@ -64,6 +64,11 @@ struct stamp_problem {
     unsigned long long last_seed = 0;
     const float* last_theta = nullptr;
     int fwd_lanes = 0, adj_lanes = 0;
+    // the bandwidth (pairwise distances + median) depends on theta only: the
+    // solves run it on a second stream beside the rollouts
+    bool overlap = true;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_theta = nullptr, ev_h = nullptr;
     // early stop of the solves, and what the last solve did
     float target = 0.f;
     int check_every = 0;
@@ -88,16 +93,20 @@ struct stamp_problem {
 namespace {
 
 template <class F>
-stamp_status timed(stamp_problem* p, int kind, F&& launch) {
+stamp_status timed_on(stamp_problem* p, int kind, cudaStream_t st, F&& launch) {
     const bool rec = p->prof && p->ev_used < p->ev_kind.size();
-    if (rec) STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used], p->stream));
+    if (rec) STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used], st));
     const cudaError_t e = launch();
     if (e != cudaSuccess) return fail(STAMP_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     if (rec) {
-        STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used + 1], p->stream));
+        STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used + 1], st));
         p->ev_kind[p->ev_used++] = kind;
     }
     return STAMP_OK;
+}
+template <class F>
+stamp_status timed(stamp_problem* p, int kind, F&& launch) {
+    return timed_on(p, kind, p->stream, launch);
 }
 
 // After a stream sync: fold the recorded event pairs into the totals.
@@ -170,9 +179,29 @@ stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
                  [&] { return stamp::launch_rollout_adj(p->sc, a, lanes, p->stream); });
 }
 
+// RBF bandwidth of theta (pairwise distances, radix-select median) on stream
+// st; h lands in p->h (and h_out when given).
+stamp_status bandwidth(stamp_problem* p, const float* theta, int N, float* h_out, cudaStream_t st) {
+    stamp::SvgdScratch s{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
+    STAMP_CUDA(cudaMemsetAsync(p->hist, 0, (2048 + 2048 + 1024) * sizeof(unsigned), st));
+    STAMP_TRY(timed_on(p, STAMP_K_PAIRWISE, st,
+                       [&] { return stamp::launch_pairwise(theta, N, p->sc.D, s, st); }));
+    if (N >= 2) {
+        for (int dg = 1; dg <= 2; ++dg)
+            STAMP_TRY(timed_on(p, STAMP_K_MEDIAN, st, [&] {
+                return stamp::launch_median_digit(N, dg, s, dg == 2 ? h_out : nullptr, st);
+            }));
+    } else if (h_out) {
+        STAMP_CUDA(cudaMemcpyAsync(h_out, p->one, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    return STAMP_OK;
+}
+
+// bw_done: the RBF bandwidth of theta is already in p->h (launched beside the
+// rollouts and waited for).
 stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, float* m, float* v,
                   int step, float lr, int sgd_phase, float* h_out, float* phi_out,
-                  const float* wn = nullptr) {
+                  const float* wn = nullptr, bool bw_done = false) {
     const int D = p->sc.D;
     const float* part = grad;   // SGD phase: phi = grad log rho, one share
     int shares = 1;
@@ -204,18 +233,7 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
         part = p->phi;
     } else if (!sgd_phase) {
         stamp::SvgdScratch s{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
-        STAMP_CUDA(cudaMemsetAsync(p->hist, 0, (2048 + 2048 + 1024) * sizeof(unsigned), p->stream));
-        STAMP_TRY(timed(p, STAMP_K_PAIRWISE,
-                        [&] { return stamp::launch_pairwise(theta, N, D, s, p->stream); }));
-        if (N >= 2) {
-            for (int dg = 1; dg <= 2; ++dg)
-                STAMP_TRY(timed(p, STAMP_K_MEDIAN, [&] {
-                    return stamp::launch_median_digit(N, dg, s, dg == 2 ? h_out : nullptr, p->stream);
-                }));
-        } else if (h_out) {
-            STAMP_CUDA(cudaMemcpyAsync(h_out, p->one, sizeof(float), cudaMemcpyDeviceToDevice,
-                                       p->stream));
-        }
+        if (!bw_done) STAMP_TRY(bandwidth(p, theta, N, h_out, p->stream));
         STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
             return stamp::launch_phi(theta, grad, N, D, s, p->phi, stamp::kMaxShares, &shares,
                                      p->stream, wn);
@@ -299,6 +317,15 @@ stamp_status run_solve(stamp_problem* p, const Phases& ph, int N, unsigned long 
     p->best_hard = INFINITY;
     for (long long it = 0; it < iters; ++it) {
         unsigned* sw = stats_out ? p->stats + it : nullptr;
+        const bool sgd = it >= (long long)ph.sur + ph.svgd;
+        // the bandwidth needs theta only: start it beside this iteration's rollouts
+        const bool side_bw = p->overlap && !sgd && p->kernel_kind == 0 && N >= 2;
+        if (side_bw) {
+            STAMP_CUDA(cudaEventRecord(p->ev_theta, p->stream));
+            STAMP_CUDA(cudaStreamWaitEvent(p->side, p->ev_theta, 0));
+            STAMP_TRY(bandwidth(p, th, N, nullptr, p->side));
+            STAMP_CUDA(cudaEventRecord(p->ev_h, p->side));
+        }
         if (it < ph.sur) {
             STAMP_TRY(timed_piece(p, STAMP_K_SURROGATE, [&] {
                 return stamp::surrogate_rollout(ph.s, p->sc, th, N, seed, (int)it, p->cost, p->grad, sw);
@@ -307,7 +334,6 @@ stamp_status run_solve(stamp_problem* p, const Phases& ph, int N, unsigned long 
             STAMP_TRY(fwd(p, th, N, seed, (int)it, 0, p->cost, nullptr, sw));
             STAMP_TRY(adj(p, th, N, p->grad));
         }
-        const bool sgd = it >= (long long)ph.sur + ph.svgd;
         const float* wn = nullptr;
         if (p->dsvgd && !sgd && it >= ph.sur) {
             // Eq. dsvgd: the hard plan of the same Gumbel draws against the relaxed one
@@ -315,8 +341,9 @@ stamp_status run_solve(stamp_problem* p, const Phases& ph, int N, unsigned long 
             STAMP_CUDA(stamp::launch_dsvgd_weights(p->cost, p->cost_hard, N, p->wn, p->stream));
             wn = p->wn;
         }
+        if (side_bw) STAMP_CUDA(cudaStreamWaitEvent(p->stream, p->ev_h, 0));
         STAMP_TRY(svgd(p, th, p->grad, N, p->m, p->v, (int)it + 1, lr, sgd ? 1 : 0, nullptr,
-                       nullptr, wn));
+                       nullptr, wn, side_bw));
         if (p->check_every > 0 && (it + 1) % p->check_every == 0) {
             STAMP_TRY(hard_min(p, th, N, seed, p->cost, &p->best_hard));
             if (p->best_hard < p->target) {
@@ -514,11 +541,18 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         off += (q.bytes + 255) / 256 * 256;
     }
     const float one = 1.f;
-    e = cudaMemcpy(p->one, &one, sizeof one, cudaMemcpyHostToDevice);
+    e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_theta, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_h, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemcpy(p->one, &one, sizeof one, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->dropped, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(p->counter, 0, 3 * sizeof(unsigned));
     if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->ev_h) cudaEventDestroy(p->ev_h);
+        if (p->ev_theta) cudaEventDestroy(p->ev_theta);
+        if (p->side) cudaStreamDestroy(p->side);
         cudaFree(p->arena);
         delete p;
         return fail(STAMP_ECUDA, "problem set-up failed: %s", cudaGetErrorString(e));
@@ -530,7 +564,11 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
 void stamp_problem_destroy(stamp_problem* p) {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
+    if (p->side) cudaStreamSynchronize(p->side);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    if (p->ev_h) cudaEventDestroy(p->ev_h);
+    if (p->ev_theta) cudaEventDestroy(p->ev_theta);
+    if (p->side) cudaStreamDestroy(p->side);
     cudaFree(p->sk_arena);
     cudaFree(p->arena);
     delete p;
@@ -633,6 +671,12 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
         return fail(STAMP_EINVAL, "negative iteration count");
     Phases ph{s, n_candidates, surrogate_iters, sim_iters, sgd_iters};
     return run_solve(p, ph, N, seed, lr, nullptr, theta_out, cost_out, k, topk_particle, stats_out);
+}
+
+stamp_status stamp_set_overlap(stamp_problem* p, int enable) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    p->overlap = enable != 0;
+    return STAMP_OK;
 }
 
 stamp_status stamp_set_svgd_kernel(stamp_problem* p, int kind) {

@@ -64,6 +64,7 @@ _sigs = {
     "stamp_set_profiling": [_vp, _i],
     "stamp_get_kernel_times": [_vp, _vp, _vp],
     "stamp_set_lanes": [_vp, _i, _i],
+    "stamp_set_overlap": [_vp, _i],
     "stamp_dropped_gradients": [_vp, _vp],
     "stamp_svgd_step_noalloc": [_vp, _vp, _i, _i, _vp, _vp, _i, _f, _i, _vp, _vp, _vp],
     "stamp_mlp_create": [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)],
@@ -290,6 +291,10 @@ class Problem:
 
     def kernel_times(self):
         return stamp_get_kernel_times(self.handle)
+
+    def set_overlap(self, enable):
+        """Bandwidth on a second stream beside the rollouts in the solves (default on)."""
+        _check(_lib.stamp_set_overlap(self.handle, int(enable)))
 
     def set_lanes(self, fwd_lanes, adj_lanes):
         stamp_set_lanes(self.handle, fwd_lanes, adj_lanes)

@@ -128,3 +128,27 @@ def test_nonfinite_initial_particles_are_reported():
     with pytest.raises(S.StampError) as e:
         gpu_solve(P, init, goal, 8, 2, 0, seed=0, theta0=theta0)
     assert e.value.status == S.STAMP_ENONFINITE
+
+
+@pytest.mark.parametrize("name,N,dsvgd", [("pusher1_h4", 300, False), ("pusher1_h2", 32, True)])
+def test_bandwidth_beside_the_rollouts_changes_nothing(name, N, dsvgd):
+    """The solves compute each iteration's bandwidth on a second stream beside
+    the rollouts; the result must be bit for bit the one-stream solve's."""
+    from paper_2310_01775_gb300 import stamp as S
+    P = W.params(name)
+    init, goal = W.scene(P, 6)
+    out = []
+    for overlap in (True, False):
+        prob = S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream)
+        prob.set_overlap(overlap)
+        prob.set_dsvgd(dsvgd)
+        th = torch.zeros(N, prob.D, device="cuda")
+        cost = torch.zeros(N, device="cuda")
+        topk = np.zeros(3, dtype=np.int32)
+        stats = np.zeros(40, dtype=np.float32)
+        prob.solve(N, 30, 10, 11, P["lr"], None, th, cost, 3, topk, stats)
+        prob.close()
+        out.append((th, cost, topk, stats))
+    (a, ca, ka, sa), (b, cb, kb, sb) = out
+    assert torch.equal(a, b) and torch.equal(ca, cb)
+    assert np.array_equal(ka, kb) and np.array_equal(sa, sb)
