@@ -101,6 +101,9 @@ struct stamp_batch {
     std::vector<long long> elem0, part0, d20, cost0, tape0;
     long long n_elem = 0;
     cudaStream_t user = nullptr, st = nullptr;
+    // the Stein bandwidths (pairwise + median) run beside the rollouts here
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<Class> cls;
     // device memory
     char* arena = nullptr;
@@ -184,14 +187,22 @@ stamp_status rollout_class(stamp_batch* b, const Class& c, bool adjoint, bool ha
     return STAMP_OK;
 }
 
-// One Stein iteration of every active instance.
+// One Stein iteration of every active instance.  The bandwidths depend on
+// the particles only: they run on the side stream beside the rollouts, and
+// the Stein direction waits for both (fork and join become graph edges when
+// captured).
 stamp_status iteration(stamp_batch* b, cudaStream_t st) {
+    B_CUDA(cudaEventRecord(b->ev_fork, st));
+    B_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+    B_CUDA(cudaMemsetAsync(b->hist, 0, b->hist_bytes, b->side));
+    B_CUDA(stamp::launch_pairwise_batch(b->sinst, b->pw_items, b->n_pw, b->max_D, b->active, b->side));
+    for (int dg = 1; dg <= 2; ++dg)
+        B_CUDA(stamp::launch_median_digit_batch(b->sinst, b->med_items, b->n_med, b->active, dg,
+                                                b->side));
+    B_CUDA(cudaEventRecord(b->ev_join, b->side));
     for (const Class& c : b->cls) B_TRY(rollout_class(b, c, false, false, st));
     for (const Class& c : b->cls) B_TRY(rollout_class(b, c, true, false, st));
-    B_CUDA(cudaMemsetAsync(b->hist, 0, b->hist_bytes, st));
-    B_CUDA(stamp::launch_pairwise_batch(b->sinst, b->pw_items, b->n_pw, b->max_D, b->active, st));
-    for (int dg = 1; dg <= 2; ++dg)
-        B_CUDA(stamp::launch_median_digit_batch(b->sinst, b->med_items, b->n_med, b->active, dg, st));
+    B_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
     B_CUDA(stamp::launch_phi_batch(b->sinst, b->phi_items, b->n_phi, b->max_D, b->active, b->flag, st));
     B_CUDA(stamp::launch_adam_batch(b->theta, b->m, b->v, b->n_elem, b->sinst, b->n, b->active, b->step,
                                     b->bc, b->lr, b->flag, st));
@@ -297,8 +308,15 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
     b->phys = phys;
     b->inst.assign(inst, inst + n_instances);
     b->user = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (b->ev_join) cudaEventDestroy(b->ev_join);
+        if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+        if (b->side) cudaStreamDestroy(b->side);
+        if (b->st) cudaStreamDestroy(b->st);
         delete b;
         return bfail(STAMP_ECUDA, "stream creation failed");
     }
@@ -344,8 +362,8 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
     for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
     if (cudaMalloc(&b->arena, total) != cudaSuccess) {
         cudaGetLastError();
-        cudaStreamDestroy(b->st);
-        delete b;
+        b->arena = nullptr;
+        stamp_batch_destroy(b);
         return bfail(STAMP_ENOMEM, "cudaMalloc of %zu bytes failed", total);
     }
     size_t off = 0;
@@ -439,12 +457,16 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
 void stamp_batch_destroy(stamp_batch* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
+    if (b->side) cudaStreamSynchronize(b->side);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (Class& c : b->cls) cudaFree(c.d_inst);
     cudaFree(b->pw_items);
     cudaFree(b->med_items);
     cudaFree(b->phi_items);
     cudaFree(b->arena);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->st) cudaStreamDestroy(b->st);
     delete b;
 }
