@@ -190,6 +190,10 @@ enum {
     STAMP_NKERNELS = 10
 };
 stamp_status stamp_set_profiling(stamp_problem* prob, int enable);
+/* The same for the kernel ids whose bit is set in mask (bit k = id k); the
+ * others launch without events.  Fewer events keep their own cost out of a
+ * timed solve.  0 stops recording. */
+stamp_status stamp_set_profiling_mask(stamp_problem* prob, unsigned mask);
 /* ms_out, launches_out: host arrays of STAMP_NKERNELS (either may be NULL). */
 stamp_status stamp_get_kernel_times(stamp_problem* prob, double* ms_out, long long* launches_out);
 

@@ -83,6 +83,7 @@ struct stamp_problem {
     float best_hard = 0.f;
     // kernel timing
     bool prof = false;
+    unsigned prof_mask = ~0u;             // kernel kinds recorded while profiling
     std::vector<cudaEvent_t> ev;          // pairs (start, stop)
     std::vector<int> ev_kind;
     size_t ev_used = 0;
@@ -94,7 +95,7 @@ namespace {
 
 template <class F>
 stamp_status timed_on(stamp_problem* p, int kind, cudaStream_t st, F&& launch) {
-    const bool rec = p->prof && p->ev_used < p->ev_kind.size();
+    const bool rec = p->prof && ((p->prof_mask >> kind) & 1u) && p->ev_used < p->ev_kind.size();
     if (rec) STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used], st));
     const cudaError_t e = launch();
     if (e != cudaSuccess) return fail(STAMP_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
@@ -259,7 +260,7 @@ struct Phases {
 // Events around a multi-launch piece (surrogate rollout, screening).
 template <class F>
 stamp_status timed_piece(stamp_problem* p, int kind, F&& piece) {
-    const bool rec = p->prof && p->ev_used < p->ev_kind.size();
+    const bool rec = p->prof && ((p->prof_mask >> kind) & 1u) && p->ev_used < p->ev_kind.size();
     if (rec) STAMP_CUDA(cudaEventRecord(p->ev[2 * p->ev_used], p->stream));
     STAMP_TRY(piece());
     if (rec) {
@@ -766,11 +767,17 @@ stamp_status stamp_dropped_gradients(stamp_problem* p, long long* count) {
 }
 
 stamp_status stamp_set_profiling(stamp_problem* p, int enable) {
+    return stamp_set_profiling_mask(p, enable ? ~0u : 0u);
+}
+
+stamp_status stamp_set_profiling_mask(stamp_problem* p, unsigned mask) {
     if (!p) return fail(STAMP_EINVAL, "NULL problem");
     STAMP_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->side) STAMP_CUDA(cudaStreamSynchronize(p->side));
     p->ev_used = 0;
     for (int q = 0; q < STAMP_NKERNELS; ++q) { p->ms[q] = 0.0; p->launches[q] = 0; }
-    p->prof = enable != 0;
+    p->prof = mask != 0;
+    p->prof_mask = mask;
     if (p->prof && p->ev.empty()) {
         constexpr size_t kPairs = 1 << 15;
         p->ev.resize(2 * kPairs);

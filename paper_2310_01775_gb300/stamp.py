@@ -62,6 +62,7 @@ _sigs = {
     "stamp_solve": [_vp, _i, _i, _i, _ull, _f, _vp, _vp, _vp, _i, _vp, _vp],
     "stamp_sync": [_vp],
     "stamp_set_profiling": [_vp, _i],
+    "stamp_set_profiling_mask": [_vp, ctypes.c_uint],
     "stamp_get_kernel_times": [_vp, _vp, _vp],
     "stamp_set_lanes": [_vp, _i, _i],
     "stamp_set_overlap": [_vp, _i],
@@ -288,6 +289,13 @@ class Problem:
 
     def set_profiling(self, enable):
         stamp_set_profiling(self.handle, enable)
+
+    def set_profiling_kernels(self, names):
+        """Record events only around the named kernels (KERNELS entries)."""
+        mask = 0
+        for n in names:
+            mask |= 1 << KERNELS.index(n)
+        _check(_lib.stamp_set_profiling_mask(self.handle, mask))
 
     def kernel_times(self):
         return stamp_get_kernel_times(self.handle)
