@@ -40,7 +40,7 @@ SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes, 1 FMA = 2
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture (profiles/rollout_pusher1_h4.md), valid while the kernel source is
 # unchanged (sha256 prefix of csrc/rollout.cuh at capture time).
-TRAFFIC = {("pusher1_h4", "rollout_adj"): ("4c1f12f3a12c38ac", 9.997056e6)}
+TRAFFIC = {("pusher1_h4", "rollout_adj"): ("b0b4b89f0df5d44d", 9.998592e6)}
 
 
 def peaks():
