@@ -139,7 +139,9 @@ __device__ __forceinline__ unsigned pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const unsigned*>(&h);
 }
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// z sigmoid(z) with the fast reciprocal (its error, a few float ulps, is far
+// below the bfloat16 rounding of the result)
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 
 // Byte offset of element (row, col) in a K-major core-matrix tile of K columns.
 __host__ __device__ __forceinline__ unsigned tile_off(int row, int col, int K) {
@@ -147,7 +149,9 @@ __host__ __device__ __forceinline__ unsigned tile_off(int row, int col, int K) {
 }
 
 constexpr int kRows = 128;                        // rows per tile (MMA M)
-constexpr int kThreads = 128;                     // 4 warps: one TMEM lane quarter each
+// 8 warps: warp w reads TMEM lane quarter w % 4 (rows 32 (w % 4) ...) and
+// takes half w / 4 of the columns in the epilogues
+constexpr int kThreads = 256;
 constexpr unsigned kTmemCols = 256;
 constexpr unsigned kActBytes = kRows * kHidden * 2;            // 64 KB
 constexpr unsigned kWBytes = kHidden * kHidden * 2;            // 128 KB
@@ -188,27 +192,28 @@ mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
     tc_fence_after();
     const unsigned tmem = sm.tmem_slot;
     unsigned tma_phase = 0, mma_phase = 0;
-    bool failed = false;
+    bool failed = false, tma_pending = false, mma_pending = false;
+    // weights of layer l (and, for l = 0, the tile's input) into shared memory
+    auto issue_load = [&](int l, int tile) {
+        const unsigned wbytes = (unsigned)(layer_n(l) * layer_k(l) * 2);
+        mbar_expect_tx(&sm.tma_bar, wbytes + (l == 0 ? kInBytes : 0u));
+        tma_load_1d(sm.w, w_tiled + layer_w_offset(l), wbytes, &sm.tma_bar);
+        if (l == 0) tma_load_1d(sm.act, x_tiled + (size_t)tile * kInBytes, kInBytes, &sm.tma_bar);
+    };
+    if (blockIdx.x < n_tiles) {
+        if (tid == 0) issue_load(0, blockIdx.x);
+        tma_pending = true;
+    }
     for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
         for (int l = 0; l < 4 && !failed; ++l) {
             const int K = layer_k(l), N = layer_n(l);
-            if (tid == 0) {
-                // act and w are free: the previous MMA has completed
-                const unsigned wbytes = (unsigned)(N * K * 2);
-                mbar_expect_tx(&sm.tma_bar, wbytes + (l == 0 ? kInBytes : 0u));
-                tma_load_1d(sm.w, w_tiled + layer_w_offset(l), wbytes, &sm.tma_bar);
-                if (l == 0) tma_load_1d(sm.act, x_tiled + (size_t)tile * kInBytes, kInBytes, &sm.tma_bar);
-            }
             unsigned spins = 0;
-            while (!mbar_try_wait(&sm.tma_bar, tma_phase) && ++spins < kWaitLimit) {
+            bool ok = true;
+            while (!(ok = mbar_try_wait(&sm.tma_bar, tma_phase)) && ++spins < kWaitLimit) {
             }
+            if (__syncthreads_or(!ok)) { failed = true; break; }   // the copy stays pending
             tma_phase ^= 1u;
-            if (__syncthreads_or(spins >= kWaitLimit)) { failed = true; break; }
-            if (saved && l > 0) {   // this layer's input activation, for the backward pass
-                unsigned char* dst = saved + ((size_t)l * tile_cap + tile_base + tile) * kActBytes;
-                for (int b = tid * 16; b < (int)kActBytes; b += kThreads * 16)
-                    *reinterpret_cast<uint4*>(dst + b) = *reinterpret_cast<const uint4*>(sm.act + b);
-            }
+            tma_pending = false;
             if (tid == 0) {
                 tc_fence_after();
                 const uint32_t idesc = idesc_bf16(kRows, N);
@@ -217,18 +222,38 @@ mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
                              smem_desc(sm.w + kk * 256, 128, (K / 8) * 128), idesc, kk > 0);
                 mma_commit(&sm.mma_bar);
             }
-            spins = 0;
-            while (!mbar_try_wait(&sm.mma_bar, mma_phase) && ++spins < kWaitLimit) {
+            mma_pending = true;
+            if (saved && l > 0) {   // this layer's input activation, for the backward pass
+                // (read beside the MMA, which only reads it too)
+                unsigned char* dst = saved + ((size_t)l * tile_cap + tile_base + tile) * kActBytes;
+                for (int b = tid * 16; b < (int)kActBytes; b += kThreads * 16)
+                    *reinterpret_cast<uint4*>(dst + b) = *reinterpret_cast<const uint4*>(sm.act + b);
             }
+            spins = 0;
+            while (!(ok = mbar_try_wait(&sm.mma_bar, mma_phase)) && ++spins < kWaitLimit) {
+            }
+            if (__syncthreads_or(!ok)) { failed = true; break; }   // the MMA stays pending
             mma_phase ^= 1u;
-            if (__syncthreads_or(spins >= kWaitLimit)) { failed = true; break; }
+            mma_pending = false;
             tc_fence_after();
-            // epilogue: this warp's 32 rows, all N columns
-            const int row = warp * 32 + lane;
-            const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+            // the weight buffer is free (and, after the last layer, the input
+            // buffer): start the next layer's (or next tile's) copy now, so it
+            // runs beside this epilogue
+            const int next_l = l < 3 ? l + 1 : 0, next_tile = l < 3 ? tile : tile + gridDim.x;
+            if (next_tile < n_tiles) {
+                if (tid == 0) {
+                    fence_async_shared();
+                    issue_load(next_l, next_tile);
+                }
+                tma_pending = true;
+            }
+            // epilogue: this warp's 32 rows, its half of the N columns
+            const int quarter = warp & 3, half = warp >> 2;
+            const int row = quarter * 32 + lane;
+            const unsigned lane_base = tmem + ((unsigned)(quarter * 32) << 16);
             const float* bl = bias + l * kHidden;
             if (l < 3) {
-                for (int c0 = 0; c0 < N; c0 += 32) {
+                for (int c0 = half * (N / 2); c0 < (half + 1) * (N / 2); c0 += 32) {
                     float v[32];
                     tmem_ld32(lane_base + c0, v);
 #pragma unroll
@@ -252,7 +277,7 @@ mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
                                 zsave + ((size_t)l * tile_cap + tile_base + tile) * kActBytes + off) = pz;
                     }
                 }
-            } else {
+            } else if (half == 0) {
                 float v[16];
                 tmem_ld16(lane_base, v);
                 const int r = tile * kRows + row;
@@ -275,10 +300,12 @@ mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
         atomicOr(err, 2);
         // a last bounded wait for the copy / MMA still in flight before the
         // tensor memory is released
-        for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.tma_bar, tma_phase ^ 1u); ++w) {
-        }
-        for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.mma_bar, mma_phase ^ 1u); ++w) {
-        }
+        if (tma_pending)
+            for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.tma_bar, tma_phase); ++w) {
+            }
+        if (mma_pending)
+            for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.mma_bar, mma_phase); ++w) {
+            }
     }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
@@ -326,7 +353,7 @@ __global__ void unpack_output_kernel(const float* __restrict__ ypad, int rows, i
 }
 
 __device__ __forceinline__ float silu_grad(float z) {
-    const float sg = 1.f / (1.f + __expf(-z));
+    const float sg = __fdividef(1.f, 1.f + __expf(-z));
     return sg * (1.f + z * (1.f - sg));
 }
 __device__ __forceinline__ float bf_lo(unsigned w) { return __uint_as_float(w << 16); }
@@ -355,13 +382,23 @@ mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = sm.tmem_slot;
-    const int row = warp * 32 + lane;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
     unsigned tma_phase = 0, mma_phase = 0;
-    bool failed = false;
+    bool failed = false, tma_pending = false, mma_pending = false;
+    auto issue_load = [&](int m) {   // W_m^T into shared memory
+        const unsigned wbytes = (unsigned)(layer_k(m) * layer_n(m) * 2);
+        mbar_expect_tx(&sm.tma_bar, wbytes);
+        tma_load_1d(sm.w, wt_tiled + layer_w_offset(m), wbytes, &sm.tma_bar);
+    };
+    if (blockIdx.x < n_tiles) {
+        if (tid == 0) issue_load(3);
+        tma_pending = true;
+    }
     for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
         const int r = tile * kRows + row;
         const size_t slot = (size_t)tile_base + tile;
-        {   // dz_3 = dy as a BF16 K-major tile of 16 columns
+        if (half == 0) {   // dz_3 = dy as a BF16 K-major tile of 16 columns
             float d[kOut];
 #pragma unroll
             for (int c = 0; c < kOut; ++c) d[c] = (r < rows && c < out_dim) ? dy[(size_t)r * out_dim + c] : 0.f;
@@ -380,16 +417,13 @@ mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
         __syncthreads();
         for (int m = 3; m >= 0 && !failed; --m) {
             const int Kb = layer_n(m), Nb = layer_k(m);   // da_m = dz_m (., Kb) W_m (Kb, Nb)
-            if (tid == 0) {
-                const unsigned wbytes = (unsigned)(Nb * Kb * 2);
-                mbar_expect_tx(&sm.tma_bar, wbytes);
-                tma_load_1d(sm.w, wt_tiled + layer_w_offset(m), wbytes, &sm.tma_bar);
-            }
             unsigned spins = 0;
-            while (!mbar_try_wait(&sm.tma_bar, tma_phase) && ++spins < kWaitLimit) {
+            bool ok = true;
+            while (!(ok = mbar_try_wait(&sm.tma_bar, tma_phase)) && ++spins < kWaitLimit) {
             }
+            if (__syncthreads_or(!ok)) { failed = true; break; }
             tma_phase ^= 1u;
-            if (__syncthreads_or(spins >= kWaitLimit)) { failed = true; break; }
+            tma_pending = false;
             if (tid == 0) {
                 tc_fence_after();
                 const uint32_t idesc = idesc_bf16(kRows, Nb);
@@ -398,17 +432,28 @@ mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
                              smem_desc(sm.w + kk * 256, 128, (Kb / 8) * 128), idesc, kk > 0);
                 mma_commit(&sm.mma_bar);
             }
+            mma_pending = true;
             spins = 0;
-            while (!mbar_try_wait(&sm.mma_bar, mma_phase) && ++spins < kWaitLimit) {
+            while (!(ok = mbar_try_wait(&sm.mma_bar, mma_phase)) && ++spins < kWaitLimit) {
             }
+            if (__syncthreads_or(!ok)) { failed = true; break; }
             mma_phase ^= 1u;
-            if (__syncthreads_or(spins >= kWaitLimit)) { failed = true; break; }
+            mma_pending = false;
             tc_fence_after();
-            const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+            // the weight buffer is free: the next layer's (or next tile's first)
+            // weights load beside this epilogue
+            if (m > 0 || tile + (int)gridDim.x < n_tiles) {
+                if (tid == 0) {
+                    fence_async_shared();
+                    issue_load(m > 0 ? m - 1 : 3);
+                }
+                tma_pending = true;
+            }
+            const unsigned lane_base = tmem + ((unsigned)(quarter * 32) << 16);
             if (m > 0) {
                 const unsigned char* zt = zsave + ((size_t)(m - 1) * tile_cap + slot) * kActBytes;
                 unsigned char* dzt = dzsave + ((size_t)(m - 1) * tile_cap + slot) * kActBytes;
-                for (int c0 = 0; c0 < kHidden; c0 += 32) {
+                for (int c0 = half * (kHidden / 2); c0 < (half + 1) * (kHidden / 2); c0 += 32) {
                     float v[32];
                     tmem_ld32(lane_base + c0, v);
 #pragma unroll
@@ -426,7 +471,7 @@ mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
                         *reinterpret_cast<uint4*>(dzt + off) = pk;
                     }
                 }
-            } else if (dx) {
+            } else if (dx && half == 0) {
                 float v[32];
                 tmem_ld32(lane_base, v);
                 if (r < rows)
@@ -439,10 +484,12 @@ mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
     }
     if (failed && tid == 0) {
         atomicOr(err, 2);
-        for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.tma_bar, tma_phase ^ 1u); ++w) {
-        }
-        for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.mma_bar, mma_phase ^ 1u); ++w) {
-        }
+        if (tma_pending)
+            for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.tma_bar, tma_phase); ++w) {
+            }
+        if (mma_pending)
+            for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.mma_bar, mma_phase); ++w) {
+            }
     }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
