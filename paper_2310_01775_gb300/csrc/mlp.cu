@@ -149,9 +149,10 @@ __host__ __device__ __forceinline__ unsigned tile_off(int row, int col, int K) {
 }
 
 constexpr int kRows = 128;                        // rows per tile (MMA M)
-// 8 warps: warp w reads TMEM lane quarter w % 4 (rows 32 (w % 4) ...) and
-// takes half w / 4 of the columns in the epilogues
-constexpr int kThreads = 256;
+// 16 warps: warp w reads TMEM lane quarter w % 4 (rows 32 (w % 4) ...) and
+// takes part w / 4 of the four column parts in the epilogues
+constexpr int kThreads = 512;
+constexpr int kParts = kThreads / 128;
 constexpr unsigned kTmemCols = 256;
 constexpr unsigned kActBytes = kRows * kHidden * 2;            // 64 KB
 constexpr unsigned kWBytes = kHidden * kHidden * 2;            // 128 KB
@@ -247,13 +248,13 @@ mlp_fwd_kernel(const unsigned char* __restrict__ x_tiled, int n_tiles,
                 }
                 tma_pending = true;
             }
-            // epilogue: this warp's 32 rows, its half of the N columns
+            // epilogue: this warp's 32 rows, its part of the N columns
             const int quarter = warp & 3, half = warp >> 2;
             const int row = quarter * 32 + lane;
             const unsigned lane_base = tmem + ((unsigned)(quarter * 32) << 16);
             const float* bl = bias + l * kHidden;
             if (l < 3) {
-                for (int c0 = half * (N / 2); c0 < (half + 1) * (N / 2); c0 += 32) {
+                for (int c0 = half * (N / kParts); c0 < (half + 1) * (N / kParts); c0 += 32) {
                     float v[32];
                     tmem_ld32(lane_base + c0, v);
 #pragma unroll
@@ -453,7 +454,7 @@ mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
             if (m > 0) {
                 const unsigned char* zt = zsave + ((size_t)(m - 1) * tile_cap + slot) * kActBytes;
                 unsigned char* dzt = dzsave + ((size_t)(m - 1) * tile_cap + slot) * kActBytes;
-                for (int c0 = half * (kHidden / 2); c0 < (half + 1) * (kHidden / 2); c0 += 32) {
+                for (int c0 = half * (kHidden / kParts); c0 < (half + 1) * (kHidden / kParts); c0 += 32) {
                     float v[32];
                     tmem_ld32(lane_base + c0, v);
 #pragma unroll
