@@ -204,6 +204,24 @@ stamp_status stamp_get_kernel_times(stamp_problem* prob, double* ms_out, long lo
  * after the other on the problem's stream.  Results are identical. */
 stamp_status stamp_set_overlap(stamp_problem* prob, int enable);
 
+/* How stamp_rollout_adjoint and the solves run the reverse sweep.
+ * STAMP_ADJ_TIME_PARALLEL (the default) applies to one-block scenes with
+ * ckpt_every = 1: the adjoint of a semi-implicit Euler substep is linear in
+ * the adjoint of the state after it, with coefficients (the Jacobian of the
+ * block's force and torque, and the linear forms of the action parameters'
+ * adjoints) that depend on the forward state only.  They are computed for
+ * every (particle, substep) pair at once from the tape, then one pass per
+ * particle runs the recurrence backwards.  Scratch: 39 floats per particle
+ * and substep, allocated at create (not when it would exceed 4 GiB).
+ * STAMP_ADJ_SEQUENTIAL: each particle's team differentiates substep after
+ * substep (segment replay for ckpt_every > 1); every other scene uses it.
+ * Both give the gradient of the same float32 simulation, with sums taken in
+ * a different order. */
+enum { STAMP_ADJ_SEQUENTIAL = 0, STAMP_ADJ_TIME_PARALLEL = 1 };
+stamp_status stamp_set_adjoint_mode(stamp_problem* prob, int mode);
+/* The mode the problem's reverse sweeps actually use. */
+stamp_status stamp_get_adjoint_mode(stamp_problem* prob, int* mode);
+
 /* Lanes per particle used by the rollout kernels (1,2,4,8,16,32; 0 = automatic). */
 stamp_status stamp_set_lanes(stamp_problem* prob, int fwd_lanes, int adj_lanes);
 

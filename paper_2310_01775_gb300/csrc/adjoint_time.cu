@@ -1,0 +1,318 @@
+// Reverse sweep of the one-block rollout as a linear recurrence in time
+// (Sec. III-B: grad log rho back-propagated through the whole trajectory).
+//
+// One semi-implicit Euler substep maps the state s = (x, y, ph, vx, vy, om)
+// through the block's total force and torque F(s) = (F_x, F_y, T) -- the M
+// relaxed-weighted pushers' contact plus ground friction:
+//   v1 = v + dt F_xy/m,  om1 = om + dt T/I,  p1 = p + dt v1,  ph1 = ph + dt om1.
+// Its adjoint is linear in the adjoint a of the state after the substep:
+//   av1 = (a_vx + dt a_x, a_vy + dt a_y, a_om + dt a_ph),
+//   a_before = (a_x, a_y, a_ph, av1) + M_t^T av1,
+//   M_t = diag(dt/m, dt/m, dt/I) dF/ds (s_t)                       (3 x 6),
+// and the action parameters' adjoints collect linear forms E_t av1: the
+// pushers' start point and displacement (through the action-start pose),
+// the offset, the distance, and each choice's weight (its unweighted force).
+// M_t and E_t depend on the forward states only.  With every state on the
+// tape (checkpoint interval 1) they are computed for all (particle, substep)
+// pairs at once (jac_kernel: throughput bound, the whole GPU busy); the
+// serial work left per particle is the recurrence itself, a few dependent
+// FMAs per substep (scan_kernel), its coefficients streamed into shared
+// memory by TMA bulk copies a window ahead.
+//
+// The contact Jacobian comes from disk_box_vjp with unit seeds -- the
+// function the sequential sweep differentiates with -- so both sweeps take
+// the same derivatives and differ only in summation order.
+#include "async_copy.cuh"
+#include "rollout.cuh"
+
+namespace stamp {
+namespace rollout {
+namespace {
+
+// Coefficients per (particle, substep): M (3 x 6, row m = force component),
+// then the forms of dPh (action-start yaw), offset, distance (3 each), then
+// the four choices' weights (3 each).
+constexpr int kM = 0, kEph = 18, kEoff = 21, kEdist = 24, kEw = 27, kCoef = 39;
+constexpr int kGroup = 8;    // particles per coefficient group (= per scan CTA)
+constexpr int kWin = 32;     // substeps per staged window
+constexpr int kRel = 6;      // relaxed parameters per action: z_0..z_3, tanh(u), sigmoid(v)
+
+// Relaxed parameters of every (particle, action), as the forward computed them.
+__global__ void relax_kernel(const SimConst sc, const RolloutArgs a, float* __restrict__ rel) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.N * sc.H) return;
+    const int i = idx % a.N, k = idx / a.N;
+    const bool noise = a.iter >= 0;
+    const uint64_t gkey = noise ? sm64(sm64(a.seed, kStreamGumbel), (uint64_t)a.iter) : 0ull;
+    float z[4], uu, vv;
+    relax_action<1>(sc, a.theta + (size_t)i * sc.D, k, i, gkey, noise, a.hard != 0, z, uu, vv);
+    float* r = rel + (size_t)k * kRel * a.N + i;
+    r[0] = z[0];
+    r[a.N] = z[1];
+    r[2 * a.N] = z[2];
+    r[3 * a.N] = z[3];
+    r[4 * a.N] = tanhf(uu);
+    r[5 * a.N] = sigmoidf_(vv);
+}
+
+// M_t and E_t of particle i at substep t, one thread per (i, t).  Output
+// layout [group i/8][t][coefficient][i%8]: a scan CTA's window is contiguous.
+__global__ void __launch_bounds__(128) jac_kernel(const SimConst sc, const RolloutArgs a,
+                                                  const float* __restrict__ rel,
+                                                  float* __restrict__ coef) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int HT = sc.H * sc.T;
+    if (idx >= (long long)a.N * HT) return;
+    const int i = (int)(idx % a.N), t = (int)(idx / a.N);
+    const int k = t / sc.T, j = t - k * sc.T;
+    const size_t ck2 = (size_t)a.N * 3;   // float2 per checkpoint (S = 6)
+    const float2* tape = reinterpret_cast<const float2*>(a.tape) + (size_t)i * 3;
+    Blocks<1> s, s0;
+    load_state(tape + (size_t)t * ck2, s);
+    load_state(tape + (size_t)(k * sc.T) * ck2, s0);   // the action's start
+    const float* r = rel + (size_t)k * kRel * a.N + i;
+    const float z[4] = {r[0], r[a.N], r[2 * a.N], r[3 * a.N]};
+    const float off = sc.off_max * r[4 * a.N];
+    const float dist = sc.dist_max * r[5 * a.N];
+    Slots<1, 1> sl;
+    make_slots<1, 1>(sc, s0, 0, z, off, dist, sl);
+    float cs[1], sn[1];
+    trig(s, cs, sn);
+    float cph0, sph0;
+    yaw_sincos(s0.ph[0], &sph0, &cph0);
+    const float j1 = (float)(j + 1), step = dist / (float)sc.T;
+
+    float J[3][6], eph[3], eoff[3], edist[3], ew[4][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        eph[m] = eoff[m] = edist[m] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) J[m][q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {   // choice q pushes side q of the block
+        const float px = sl.p0x[q] + j1 * sl.dx[q], py = sl.p0y[q] + j1 * sl.dy[q];
+        const float vpx = sl.dx[q] * sc.inv_dt, vpy = sl.dy[q] * sc.inv_dt;
+        // pusher start point p0 = pos + R l and displacement -R n dist/T at the action start
+        float nx, ny;
+        side_normal(q, nx, ny);
+        const float tx = -ny, ty = nx;
+        const float lx = nx * (sc.hs + sc.r) + tx * off;
+        const float ly = ny * (sc.hs + sc.r) + ty * off;
+        const float dRl_x = -sph0 * lx - cph0 * ly, dRl_y = cph0 * lx - sph0 * ly;
+        const float dRn_x = -sph0 * nx - cph0 * ny, dRn_y = cph0 * nx - sph0 * ny;
+        const float ux = -(cph0 * nx - sph0 * ny), uy = -(sph0 * nx + cph0 * ny);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const DiskGrad g = disk_box_vjp(sc, px, py, vpx, vpy, s.x[0], s.y[0], cs[0], sn[0],
+                                            s.vx[0], s.vy[0], s.om[0], sl.w[q], m == 0 ? 1.f : 0.f,
+                                            m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f);
+            J[m][0] += g.bx;
+            J[m][1] += g.by;
+            J[m][2] += g.ph;
+            J[m][3] += g.vx;
+            J[m][4] += g.vy;
+            J[m][5] += g.om;
+            const float adx = j1 * g.px + g.vpx * sc.inv_dt, ady = j1 * g.py + g.vpy * sc.inv_dt;
+            eph[m] += g.px * dRl_x + g.py * dRl_y - (adx * dRn_x + ady * dRn_y) * step;
+            eoff[m] += (cph0 * g.px + sph0 * g.py) * tx + (-sph0 * g.px + cph0 * g.py) * ty;
+            edist[m] += (adx * ux + ady * uy) / (float)sc.T;
+            ew[q][m] = g.w;
+        }
+    }
+    // ground friction -fl v/sqrt(|v|^2+eps_v^2), -fa om/sqrt(om^2+eps_w^2)
+    const float vx = s.vx[0], vy = s.vy[0], om = s.om[0];
+    const float isv = rsqrtf(vx * vx + vy * vy + sc.eps_v2);
+    const float iso = rsqrtf(om * om + sc.eps_w2);
+    const float isv3 = isv * isv * isv;
+    J[0][3] -= sc.fric_lin * (isv - vx * vx * isv3);
+    J[1][3] += sc.fric_lin * vx * vy * isv3;
+    J[0][4] += sc.fric_lin * vx * vy * isv3;
+    J[1][4] -= sc.fric_lin * (isv - vy * vy * isv3);
+    J[2][5] -= sc.fric_ang * sc.eps_w2 * (iso * iso * iso);
+
+    const float cm[3] = {sc.dt * sc.inv_m, sc.dt * sc.inv_m, sc.dt * sc.inv_I};
+    const int grp = i / kGroup, p = i % kGroup;
+    float* out = coef + ((size_t)grp * HT + t) * kCoef * kGroup + p;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) out[(kM + 6 * m + q) * kGroup] = cm[m] * J[m][q];
+        out[(kEph + m) * kGroup] = cm[m] * eph[m];
+        out[(kEoff + m) * kGroup] = cm[m] * eoff[m];
+        out[(kEdist + m) * kGroup] = cm[m] * edist[m];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[(kEw + 3 * q + m) * kGroup] = cm[m] * ew[q][m];
+    }
+}
+
+// The recurrence, backwards over the H*T substeps: one CTA of 8 particles,
+// a team of 4 lanes per particle.  Every lane carries the state adjoint
+// (redundantly); lane l also accumulates choice l's weight form, and lanes
+// 0, 1, 2 the action-start yaw, offset and distance forms.  Window w of the
+// coefficients is copied into buffer w%2 while window w-1 is consumed.
+struct ScanSmem {
+    uint64_t bar[2];
+    float pad[28];   // the buffers start 128 B in
+    float buf[2][kWin * kCoef * kGroup];
+};
+
+__global__ void __launch_bounds__(32) scan_kernel(const SimConst sc, const RolloutArgs a,
+                                                  const float* __restrict__ rel,
+                                                  const float* __restrict__ coef,
+                                                  int* __restrict__ flag) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    ScanSmem& sm = *reinterpret_cast<ScanSmem*>(smem_raw);
+    const int tid = threadIdx.x, p = tid >> 2, lane = tid & 3;
+    const int grp = blockIdx.x;
+    int i = grp * kGroup + p;
+    const bool on = i < a.N;
+    if (!on) i = a.N - 1;   // surplus team: shadows the last particle, writes nothing
+    const int T = sc.T, HT = sc.H * sc.T;
+    const int nwin = (HT + kWin - 1) / kWin;
+    const float* cgrp = coef + (size_t)grp * HT * kCoef * kGroup;
+    // window w covers substeps [lo(w), hi(w)), counted from the end
+    auto lo = [&](int w) { return max(0, HT - (w + 1) * kWin); };
+    auto hi = [&](int w) { return HT - w * kWin; };
+    auto issue = [&](int w) {
+        const unsigned bytes = (unsigned)((hi(w) - lo(w)) * kCoef * kGroup * sizeof(float));
+        async::mbar_expect_tx(&sm.bar[w & 1], bytes);
+        async::tma_load_1d(sm.buf[w & 1], cgrp + (size_t)lo(w) * kCoef * kGroup, bytes,
+                           &sm.bar[w & 1]);
+    };
+    if (tid == 0) {
+        async::mbar_init(&sm.bar[0], 1);
+        async::mbar_init(&sm.bar[1], 1);
+        async::fence_async_shared();
+    }
+    __syncthreads();
+    bool pending[2] = {true, nwin > 1};
+    unsigned parity[2] = {0u, 0u};
+    if (tid == 0) {
+        issue(0);
+        if (nwin > 1) issue(1);
+    }
+
+    // adjoint of the cost at the final state
+    const float2* tape = reinterpret_cast<const float2*>(a.tape) + (size_t)i * 3;
+    Blocks<1> sf;
+    load_state(tape + (size_t)sc.n_ckpt * a.N * 3, sf);
+    float ax = 2.f * (sf.x[0] - sc.goal[0][0]);
+    float ay = 2.f * (sf.y[0] - sc.goal[0][1]);
+    float aph = 2.f * sc.w_yaw * wrapf(sf.ph[0] - sc.goal[0][2]);
+    float avx = 0.f, avy = 0.f, aom = 0.f;
+
+    const int fe = kEph + 3 * (lane < 3 ? lane : 0);   // lane 3 repeats lane 0's form, unused
+    const int fw = kEw + 3 * lane;
+    float dX = 0.f, dY = 0.f, e = 0.f, az = 0.f;
+    bool bad = false, failed = false;
+    int k = sc.H - 1, j = T - 1;
+    const bool hard = a.hard != 0;
+    for (int w = 0; w < nwin; ++w) {
+        const int b = w & 1;
+        bool ok;
+        unsigned spins = 0;
+        while (!(ok = async::mbar_try_wait(&sm.bar[b], parity[b])) && ++spins < async::kWaitLimit) {
+        }
+        if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }   // the copy stays pending
+        parity[b] ^= 1u;
+        pending[b] = false;
+        const int l0 = lo(w);
+        for (int t = hi(w) - 1; t >= l0; --t) {
+            const float* c = sm.buf[b] + (t - l0) * kCoef * kGroup + p;
+            const float v0 = avx + sc.dt * ax, v1 = avy + sc.dt * ay, v2 = aom + sc.dt * aph;
+            float d[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                d[q] = c[(kM + q) * kGroup] * v0 + c[(kM + 6 + q) * kGroup] * v1 +
+                       c[(kM + 12 + q) * kGroup] * v2;
+            ax += d[0];
+            ay += d[1];
+            aph += d[2];
+            avx = v0 + d[3];
+            avy = v1 + d[4];
+            aom = v2 + d[5];
+            dX -= d[0];   // the pushers move with the block's start position
+            dY -= d[1];
+            e += c[fe * kGroup] * v0 + c[(fe + 1) * kGroup] * v1 + c[(fe + 2) * kGroup] * v2;
+            az += c[fw * kGroup] * v0 + c[(fw + 1) * kGroup] * v1 + c[(fw + 2) * kGroup] * v2;
+            if (j > 0) { --j; continue; }
+            // start of action k: the pushers' placement, then the parameter gradient
+            const int base = tid & ~3;
+            const float dph = __shfl_sync(0xffffffffu, e, base);
+            const float aoff = __shfl_sync(0xffffffffu, e, base + 1);
+            float adist = __shfl_sync(0xffffffffu, e, base + 2);
+            ax += dX;
+            ay += dY;
+            aph += dph;
+            const float* r = rel + (size_t)k * kRel * a.N + i;
+            const float zl = r[lane * a.N], tu = r[4 * a.N], sg = r[5 * a.N];
+            adist += 2.f * sc.w_push * (sc.dist_max * sg);
+            const float zaz = team_sum<4>(zl * az);
+            if (on) {
+                float* gr = a.grad + (size_t)i * sc.D + (size_t)k * 6;
+                const float gz = hard ? 0.f : -(zl * (az - zaz) * sc.inv_tau);
+                gr[lane] = gz;
+                bad |= !isfinite(gz);
+                if (lane == 0) {
+                    const float gv = -(aoff * sc.off_max * (1.f - tu * tu));
+                    gr[4] = gv;
+                    bad |= !isfinite(gv);
+                }
+                if (lane == 1) {
+                    const float gv = -(adist * sc.dist_max * sg * (1.f - sg));
+                    gr[5] = gv;
+                    bad |= !isfinite(gv);
+                }
+            }
+            dX = dY = e = az = 0.f;
+            --k;
+            j = T - 1;
+        }
+        __syncwarp();
+        if (w + 2 < nwin) {   // the buffer is free again
+            if (tid == 0) issue(w + 2);
+            pending[b] = true;
+        }
+    }
+    if (failed) {
+        if (tid == 0) atomicOr(flag, 2);
+        for (int b = 0; b < 2; ++b)   // let the copies in flight land before the CTA exits
+            for (unsigned s = 0; pending[b] && s < async::kWaitLimit; ++s)
+                if (async::mbar_try_wait(&sm.bar[b], parity[b])) break;
+        return;
+    }
+    // an overflowed reverse sweep gives the particle a zero gradient, and is counted
+    bad = team_sum<4>(bad ? 1.f : 0.f) > 0.f;
+    if (on && bad) {
+        for (int q = lane; q < sc.D; q += 4) a.grad[(size_t)i * sc.D + q] = 0.f;
+        if (lane == 0 && a.dropped) atomicAdd(a.dropped, 1ull);
+    }
+}
+
+constexpr size_t kScanSmem = sizeof(ScanSmem);
+
+}  // namespace
+}  // namespace rollout
+
+size_t adjoint_time_coef_floats(int n, int H, int T) {
+    return (size_t)((n + rollout::kGroup - 1) / rollout::kGroup) * rollout::kGroup * H * T *
+           rollout::kCoef;
+}
+size_t adjoint_time_rel_floats(int n, int H) { return (size_t)n * H * rollout::kRel; }
+
+cudaError_t launch_adjoint_time(const SimConst& sc, const RolloutArgs& a, float* rel, float* coef,
+                                int* flag, cudaStream_t st) {
+    using namespace rollout;
+    if (sc.nb != 1 || sc.C != 1 || a.N < 1) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kScanSmem);
+    if (e != cudaSuccess) return e;
+    const long long pairs = (long long)a.N * sc.H * sc.T;
+    relax_kernel<<<(a.N * sc.H + 127) / 128, 128, 0, st>>>(sc, a, rel);
+    jac_kernel<<<(unsigned)((pairs + 127) / 128), 128, 0, st>>>(sc, a, rel, coef);
+    scan_kernel<<<(a.N + kGroup - 1) / kGroup, 32, kScanSmem, st>>>(sc, a, rel, coef, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace stamp

@@ -35,6 +35,9 @@ stamp_status fail(stamp_status s, const char* fmt, ...) {
 
 constexpr int kMaxParticles = 16384;     // d2 scratch is N^2 floats (1 GiB at the cap)
 constexpr long long kMaxStatsIters = 1 << 20;
+// the time-parallel reverse sweep keeps 39 coefficients per particle and
+// substep; above this it is not set up (the sequential sweep runs)
+constexpr size_t kMaxTimeParallelBytes = (size_t)4 << 30;
 
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes at;
@@ -64,6 +67,11 @@ struct stamp_problem {
     unsigned long long last_seed = 0;
     const float* last_theta = nullptr;
     int fwd_lanes = 0, adj_lanes = 0;
+    // one-block reverse sweep as a linear recurrence in time (checkpoint
+    // interval 1): its scratch exists when the problem qualifies
+    int adj_mode = STAMP_ADJ_TIME_PARALLEL;
+    float *pit_rel = nullptr, *pit_coef = nullptr;
+    bool pit_ok = false;
     // the bandwidth (pairwise distances + median) depends on theta only: the
     // solves run it on a second stream beside the rollouts
     bool overlap = true;
@@ -175,6 +183,10 @@ stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
     stamp::RolloutArgs a{};
     a.theta = theta; a.N = N; a.seed = p->last_seed; a.iter = p->last_iter; a.hard = p->last_hard;
     a.tape = p->tape; a.grad = grad; a.dropped = p->dropped;
+    if (p->adj_mode == STAMP_ADJ_TIME_PARALLEL && p->pit_ok)
+        return timed(p, STAMP_K_ROLLOUT_ADJ, [&] {
+            return stamp::launch_adjoint_time(p->sc, a, p->pit_rel, p->pit_coef, p->flag, p->stream);
+        });
     const int lanes = lanes_for(p, N, true);
     return timed(p, STAMP_K_ROLLOUT_ADJ,
                  [&] { return stamp::launch_rollout_adj(p->sc, a, lanes, p->stream); });
@@ -505,6 +517,8 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
 
     // carve the arena
     const size_t n = (size_t)max_particles;
+    const size_t pit_coef_bytes = stamp::adjoint_time_coef_floats(max_particles, sc.H, sc.T) * sizeof(float);
+    const bool pit = sc.nb == 1 && sc.C == 1 && pit_coef_bytes <= kMaxTimeParallelBytes;
     struct Part { void** dst; size_t bytes; };
     const Part parts[] = {
         {(void**)&p->tape, (size_t)(sc.n_ckpt + 1) * n * sc.S * sizeof(float)},
@@ -527,7 +541,10 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         {(void**)&p->stop, sizeof(unsigned)},
         {(void**)&p->cost_hard, n * sizeof(float)},
         {(void**)&p->wn, n * sizeof(float)},
+        {(void**)&p->pit_rel, pit ? stamp::adjoint_time_rel_floats(max_particles, sc.H) * sizeof(float) : 0},
+        {(void**)&p->pit_coef, pit ? pit_coef_bytes : 0},
     };
+    p->pit_ok = pit;
     size_t total = 0;
     for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
     cudaError_t e = cudaMalloc(&p->arena, total);
@@ -672,6 +689,21 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
         return fail(STAMP_EINVAL, "negative iteration count");
     Phases ph{s, n_candidates, surrogate_iters, sim_iters, sgd_iters};
     return run_solve(p, ph, N, seed, lr, nullptr, theta_out, cost_out, k, topk_particle, stats_out);
+}
+
+stamp_status stamp_set_adjoint_mode(stamp_problem* p, int mode) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    if (mode != STAMP_ADJ_SEQUENTIAL && mode != STAMP_ADJ_TIME_PARALLEL)
+        return fail(STAMP_EINVAL, "adjoint mode must be STAMP_ADJ_SEQUENTIAL or STAMP_ADJ_TIME_PARALLEL");
+    p->adj_mode = mode;
+    return STAMP_OK;
+}
+
+stamp_status stamp_get_adjoint_mode(stamp_problem* p, int* mode) {
+    if (!p || !mode) return fail(STAMP_EINVAL, "NULL problem or mode");
+    *mode = (p->adj_mode == STAMP_ADJ_TIME_PARALLEL && p->pit_ok) ? STAMP_ADJ_TIME_PARALLEL
+                                                                  : STAMP_ADJ_SEQUENTIAL;
+    return STAMP_OK;
 }
 
 stamp_status stamp_set_overlap(stamp_problem* p, int enable) {

@@ -108,6 +108,14 @@ cudaError_t launch_rollout_nb2(const SimConst&, const RolloutArgs&, int, bool, c
 cudaError_t launch_rollout_nb3(const SimConst&, const RolloutArgs&, int, bool, cudaStream_t);
 cudaError_t launch_rollout_nb4(const SimConst&, const RolloutArgs&, int, bool, cudaStream_t);
 
+// One-block reverse sweep as a linear recurrence in time (adjoint_time.cu),
+// for checkpoint interval 1: rel and coef of the sizes below (floats) for up
+// to n particles; flag receives bit 2 if a staged copy never lands.
+size_t adjoint_time_coef_floats(int n, int H, int T);
+size_t adjoint_time_rel_floats(int n, int H);
+cudaError_t launch_adjoint_time(const SimConst& sc, const RolloutArgs& a, float* rel, float* coef,
+                                int* flag, cudaStream_t st);
+
 // SVGD step pieces (svgd.cu).  Scratch buffers are owned by the problem.
 struct SvgdScratch {
     float* d2;            // N x N squared distances

@@ -32,13 +32,15 @@ def setup(name, over, N, seed):
     return P, init, goal, M, D, theta
 
 
-def gpu_rollout(P, init, goal, theta, seed, it, lanes=None, hard=0):
+def gpu_rollout(P, init, goal, theta, seed, it, lanes=None, hard=0, adj_mode=None):
     from paper_2310_01775_gb300 import stamp as S
     dev = torch.device("cuda:0")
     N, D = theta.shape
     prob = S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream)
     if lanes:
         prob.set_lanes(lanes, lanes)
+    if adj_mode is not None:
+        prob.set_adjoint_mode(adj_mode)
     th = torch.tensor(theta, device=dev)
     cost = torch.empty(N, device=dev)
     fin = torch.empty(N, prob.S, device=dev)
@@ -145,6 +147,13 @@ def test_full_size_sampled_particles(name, sample):
     few = idx[:12]
     whole = Reference(theta[few], P, init, goal, gum[:12], C=C)
     whole.check(tape[few], fin[few], cost[few], grad[few], min_frac=0.0)
+    if P["n_blocks"] == 1 and C == 1:
+        # the default sweep here is the time-parallel one; the sequential
+        # sweep on the same tape sums the same derivatives in another order:
+        # over all particles (chaotic ones included) the median gap stays far
+        # below the gradient bar
+        _, _, _, g_seq = gpu_rollout(P, init, goal, theta, seed, it, adj_mode=0)
+        assert np.median(rel_err(grad, g_seq)) < 1e-4
 
 
 def test_adjoint_requires_matching_forward():
@@ -165,3 +174,68 @@ def test_adjoint_requires_matching_forward():
     with pytest.raises(S.StampError):
         prob.rollout_fwd(th.cpu(), 8, seed, 0, 0, c)     # host theta
     prob.close()
+
+
+# one-block, checkpoint-interval-1 cases: both reverse sweeps apply
+ONE_BLOCK_C1 = [
+    ("pusher1_h2", dict(H=1, ckpt_every=1), 37, 4, 0.3),
+    ("pusher1_h2", dict(ckpt_every=1), 32, 2, 0.3),
+    ("pusher1_h2", dict(SOFT, ckpt_every=1), 40, 4, 1.0),
+    ("pusher1_h4", dict(SOFT), 40, 1, 1.0),
+    ("pusher1_h4", dict(SOFT), 9, 4, 1.0),        # one partial group of 8
+]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name,over,N,lanes,min_frac", ONE_BLOCK_C1)
+def test_both_reverse_sweeps_meet_the_bar(name, over, N, lanes, min_frac, mode):
+    """Sequential (0) and time-parallel (1) reverse sweeps against the FP64
+    oracle, and against each other on the same tape: the same derivatives
+    summed in another order."""
+    seed, it = 5, 3
+    P, init, goal, M, D, theta = setup(name, over, N, seed)
+    cost, fin, tape, grad = gpu_rollout(P, init, goal, theta, seed, it, lanes, adj_mode=mode)
+    gum = O.gumbel_noise(seed, it, N, P["H"], M)
+    ref = Reference(theta, P, init, goal, gum, C=1)
+    ok = ref.check(tape, fin, cost, grad, min_frac=min_frac)
+    _, _, _, other = gpu_rollout(P, init, goal, theta, seed, it, lanes, adj_mode=1 - mode)
+    assert rel_err(grad, other)[ok].max(initial=0) < 1e-4
+
+
+def test_hard_rollout_time_parallel_gradient_has_no_logit_term():
+    """The hard map's one-hot choice has no gradient; offset and distance do."""
+    seed, it, N = 3, -1, 16
+    P, init, goal, M, D, theta = setup("pusher1_h2", dict(SOFT, ckpt_every=1), N, seed)
+    from paper_2310_01775_gb300 import stamp as S
+    prob = S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream)
+    assert prob.adjoint_mode() == S.STAMP_ADJ_TIME_PARALLEL
+    th = torch.tensor(theta, device="cuda")
+    c = torch.empty(N, device="cuda")
+    g = torch.empty(N, D, device="cuda")
+    g0 = torch.empty(N, D, device="cuda")
+    prob.rollout_fwd(th, N, seed, it, 1, c)
+    prob.rollout_adjoint(th, N, seed, it, g)
+    prob.set_adjoint_mode(S.STAMP_ADJ_SEQUENTIAL)
+    prob.rollout_adjoint(th, N, seed, it, g0)
+    prob.sync()
+    prob.close()
+    g, g0 = g.cpu().numpy().reshape(N, P["H"], M + 2), g0.cpu().numpy().reshape(N, P["H"], M + 2)
+    assert np.abs(g[:, :, :M]).max() == 0.0 and np.abs(g0[:, :, :M]).max() == 0.0
+    assert np.abs(g[:, :, M:]).max() > 0.0
+    assert np.median(rel_err(g, g0)) < 1e-5
+
+
+def test_adjoint_mode_where_it_applies():
+    from paper_2310_01775_gb300 import stamp as S
+    for name, over, want in [("pusher1_h2", dict(ckpt_every=1), S.STAMP_ADJ_TIME_PARALLEL),
+                             ("pusher1_h2", dict(ckpt_every=25), S.STAMP_ADJ_SEQUENTIAL),
+                             ("pusher3_h6", dict(H=1, ckpt_every=1), S.STAMP_ADJ_SEQUENTIAL)]:
+        P = W.params(name, **over)
+        init, goal = W.scene(P, 0)
+        prob = S.Problem(P, init, goal, 8, torch.cuda.current_stream().cuda_stream)
+        assert prob.adjoint_mode() == want, (name, over)
+        prob.set_adjoint_mode(S.STAMP_ADJ_SEQUENTIAL)
+        assert prob.adjoint_mode() == S.STAMP_ADJ_SEQUENTIAL
+        with pytest.raises(S.StampError):
+            prob.set_adjoint_mode(7)
+        prob.close()
