@@ -205,22 +205,26 @@ stamp_status stamp_get_kernel_times(stamp_problem* prob, double* ms_out, long lo
 stamp_status stamp_set_overlap(stamp_problem* prob, int enable);
 
 /* How stamp_rollout_adjoint and the solves run the reverse sweep.
- * STAMP_ADJ_TIME_PARALLEL (the default) applies to one-block scenes with
- * ckpt_every = 1: the adjoint of a semi-implicit Euler substep is linear in
- * the adjoint of the state after it, with coefficients (the Jacobian of the
- * block's force and torque, and the linear forms of the action parameters'
- * adjoints) that depend on the forward state only.  They are computed for
- * every (particle, substep) pair at once from the tape, then one pass per
- * particle runs the recurrence backwards.  Scratch: 39 floats per particle
- * and substep, allocated at create (not when it would exceed 4 GiB).
+ * STAMP_ADJ_TIME_PARALLEL applies to one-block scenes with ckpt_every = 1:
+ * the adjoint of a semi-implicit Euler substep is linear in the adjoint of
+ * the state after it, with coefficients (the Jacobian of the block's force
+ * and torque, and the linear forms of the action parameters' adjoints) that
+ * depend on the forward state only.  They are computed for every (particle,
+ * substep) pair at once from the tape; then one short recurrence per
+ * particle runs backwards.  Scratch: 44 floats per particle and substep,
+ * allocated at create (not when it would exceed 4 GiB).
  * STAMP_ADJ_SEQUENTIAL: each particle's team differentiates substep after
  * substep (segment replay for ckpt_every > 1); every other scene uses it.
- * Both give the gradient of the same float32 simulation, with sums taken in
- * a different order. */
-enum { STAMP_ADJ_SEQUENTIAL = 0, STAMP_ADJ_TIME_PARALLEL = 1 };
+ * STAMP_ADJ_AUTO (the default): time-parallel where it applies, for up to
+ * 3072 particles (beyond that the sequential teams fill the GPU and the
+ * Jacobians' extra arithmetic costs more than it saves), else sequential.
+ * Both sweeps give the gradient of the same float32 simulation, with sums
+ * taken in a different order. */
+enum { STAMP_ADJ_SEQUENTIAL = 0, STAMP_ADJ_TIME_PARALLEL = 1, STAMP_ADJ_AUTO = 2 };
 stamp_status stamp_set_adjoint_mode(stamp_problem* prob, int mode);
-/* The mode the problem's reverse sweeps actually use. */
-stamp_status stamp_get_adjoint_mode(stamp_problem* prob, int* mode);
+/* The sweep (STAMP_ADJ_SEQUENTIAL or STAMP_ADJ_TIME_PARALLEL) that a call
+ * with N particles uses. */
+stamp_status stamp_get_adjoint_mode(stamp_problem* prob, int N, int* mode);
 
 /* Lanes per particle used by the rollout kernels (1,2,4,8,16,32; 0 = automatic). */
 stamp_status stamp_set_lanes(stamp_problem* prob, int fwd_lanes, int adj_lanes);

@@ -14,10 +14,10 @@
 // the offset, the distance, and each choice's weight (its unweighted force).
 // M_t and E_t depend on the forward states only.  With every state on the
 // tape (checkpoint interval 1) they are computed for all (particle, substep)
-// pairs at once (jac_kernel: throughput bound, the whole GPU busy); the
-// serial work left per particle is the recurrence itself, a few dependent
-// FMAs per substep (scan_kernel), its coefficients streamed into shared
-// memory by TMA bulk copies a window ahead.
+// pairs at once (jac_kernel: throughput bound, the whole GPU busy); what
+// stays serial per particle is the recurrence itself, a few dependent FMAs
+// per substep (scan_kernel, its coefficients streamed into shared memory by
+// TMA bulk copies a window ahead).
 //
 // The contact Jacobian comes from disk_box_vjp with unit seeds -- the
 // function the sequential sweep differentiates with -- so both sweeps take
@@ -29,13 +29,123 @@ namespace stamp {
 namespace rollout {
 namespace {
 
-// Coefficients per (particle, substep): M (3 x 6, row m = force component),
-// then the forms of dPh (action-start yaw), offset, distance (3 each), then
-// the four choices' weights (3 each).
-constexpr int kM = 0, kEph = 18, kEoff = 21, kEdist = 24, kEw = 27, kCoef = 39;
-constexpr int kGroup = 8;    // particles per coefficient group (= per scan CTA)
-constexpr int kWin = 32;     // substeps per staged window
-constexpr int kRel = 6;      // relaxed parameters per action: z_0..z_3, tanh(u), sigmoid(v)
+// Coefficient row of one (particle, substep): 44 floats (176 B):
+//   [0, 18)   M, row m (F_x, F_y, T) of 6 state columns
+//   [18, 20)  zero
+//   [20 + 6l, 26 + 6l), l = 0..3: the scan's lane l reads form l -- the
+//             action-start yaw (l = 0), offset (1), distance (2), none
+//             (3: zero) -- then the weight form of choice l (3 floats each)
+// Rows are grouped [particle / 8][substep][particle % 8]: a scan CTA's
+// window of substeps is one contiguous span.
+constexpr int kRow = 44, kE = 20;
+constexpr int kGroup = 8;      // particles per coefficient group (= per scan CTA)
+constexpr int kWin = 32;       // substeps per staged window of the scan
+constexpr int kRel = 6;        // relaxed parameters per action: z_0..z_3, tanh(u), sigmoid(v)
+
+// Item q's weighted contact Jacobian (rows F_x, F_y, T; columns the state)
+// and its forms, at one substep, per unit adjoint of each force component.
+struct ItemJac {
+    float J[3][6];
+    float eph[3], eoff[3], edist[3], ew[3];
+};
+
+__device__ __forceinline__ void item_jac(const SimConst& sc, const Blocks<1>& s, float cs, float sn,
+                                         int q, float p0x, float p0y, float dxq, float dyq,
+                                         float w, float j1, float step, float cph0, float sph0,
+                                         float off, ItemJac& o) {
+    const float px = p0x + j1 * dxq, py = p0y + j1 * dyq;
+    const float vpx = dxq * sc.inv_dt, vpy = dyq * sc.inv_dt;
+    // pusher start point p0 = pos + R l and displacement -R n dist/T at the action start
+    float nx, ny;
+    side_normal(q, nx, ny);
+    const float tx = -ny, ty = nx;
+    const float lx = nx * (sc.hs + sc.r) + tx * off;
+    const float ly = ny * (sc.hs + sc.r) + ty * off;
+    const float dRl_x = -sph0 * lx - cph0 * ly, dRl_y = cph0 * lx - sph0 * ly;
+    const float dRn_x = -sph0 * nx - cph0 * ny, dRn_y = cph0 * nx - sph0 * ny;
+    const float ux = -(cph0 * nx - sph0 * ny), uy = -(sph0 * nx + cph0 * ny);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const DiskGrad g = disk_box_vjp(sc, px, py, vpx, vpy, s.x[0], s.y[0], cs, sn, s.vx[0],
+                                        s.vy[0], s.om[0], w, m == 0 ? 1.f : 0.f,
+                                        m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f);
+        o.J[m][0] = g.bx;
+        o.J[m][1] = g.by;
+        o.J[m][2] = g.ph;
+        o.J[m][3] = g.vx;
+        o.J[m][4] = g.vy;
+        o.J[m][5] = g.om;
+        const float adx = j1 * g.px + g.vpx * sc.inv_dt, ady = j1 * g.py + g.vpy * sc.inv_dt;
+        o.eph[m] = g.px * dRl_x + g.py * dRl_y - (adx * dRn_x + ady * dRn_y) * step;
+        o.eoff[m] = (cph0 * g.px + sph0 * g.py) * tx + (-sph0 * g.px + cph0 * g.py) * ty;
+        o.edist[m] = (adx * ux + ady * uy) / (float)sc.T;
+        o.ew[m] = g.w;
+    }
+}
+
+// Ground friction -fl v/sqrt(|v|^2+eps_v^2), -fa om/sqrt(om^2+eps_w^2): its
+// part of the Jacobian.
+__device__ __forceinline__ void friction_jac(const SimConst& sc, const Blocks<1>& s,
+                                             float (&J)[3][6]) {
+    const float vx = s.vx[0], vy = s.vy[0], om = s.om[0];
+    const float isv = rsqrtf(vx * vx + vy * vy + sc.eps_v2);
+    const float iso = rsqrtf(om * om + sc.eps_w2);
+    const float isv3 = isv * isv * isv;
+    J[0][3] -= sc.fric_lin * (isv - vx * vx * isv3);
+    J[1][3] += sc.fric_lin * vx * vy * isv3;
+    J[0][4] += sc.fric_lin * vx * vy * isv3;
+    J[1][4] -= sc.fric_lin * (isv - vy * vy * isv3);
+    J[2][5] -= sc.fric_ang * sc.eps_w2 * (iso * iso * iso);
+}
+
+__device__ __forceinline__ float* coef_row(float* coef, int HT, int i, int t) {
+    return coef + (((size_t)(i / kGroup) * HT + t) * kGroup + i % kGroup) * kRow;
+}
+
+// The coefficient row of one (particle, substep) from its state (with the
+// yaw's cos/sin) and its action's pushers (start point, displacement and
+// weight of the four items; cos/sin of the start yaw; offset).
+__device__ __forceinline__ void pair_row(const SimConst& sc, const Blocks<1>& s, float cs, float sn,
+                                         const float (&p0x)[4], const float (&p0y)[4],
+                                         const float (&dx)[4], const float (&dy)[4],
+                                         const float (&w)[4], float j1, float step, float cph0,
+                                         float sph0, float off, float (&row)[kRow]) {
+    float J[3][6], eph[3], eoff[3], edist[3], ew[4][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        eph[m] = eoff[m] = edist[m] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) J[m][c] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {   // choice q pushes side q of the block
+        ItemJac o;
+        item_jac(sc, s, cs, sn, q, p0x[q], p0y[q], dx[q], dy[q], w[q], j1, step, cph0, sph0, off, o);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) J[m][c] += o.J[m][c];
+            eph[m] += o.eph[m];
+            eoff[m] += o.eoff[m];
+            edist[m] += o.edist[m];
+            ew[q][m] = o.ew[m];
+        }
+    }
+    friction_jac(sc, s, J);
+    const float cm[3] = {sc.dt * sc.inv_m, sc.dt * sc.inv_m, sc.dt * sc.inv_I};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) row[6 * m + c] = cm[m] * J[m][c];
+        row[kE + m] = cm[m] * eph[m];
+        row[kE + 6 + m] = cm[m] * eoff[m];
+        row[kE + 12 + m] = cm[m] * edist[m];
+        row[kE + 18 + m] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) row[kE + 6 * q + 3 + m] = cm[m] * ew[q][m];
+    }
+    row[18] = row[19] = 0.f;
+}
 
 // Relaxed parameters of every (particle, action), as the forward computed them.
 __global__ void relax_kernel(const SimConst sc, const RolloutArgs a, float* __restrict__ rel) {
@@ -55,8 +165,7 @@ __global__ void relax_kernel(const SimConst sc, const RolloutArgs a, float* __re
     r[5 * a.N] = sigmoidf_(vv);
 }
 
-// M_t and E_t of particle i at substep t, one thread per (i, t).  Output
-// layout [group i/8][t][coefficient][i%8]: a scan CTA's window is contiguous.
+// The coefficients of particle i at substep t from the tape, one thread per (i, t).
 __global__ void __launch_bounds__(128) jac_kernel(const SimConst sc, const RolloutArgs a,
                                                   const float* __restrict__ rel,
                                                   float* __restrict__ coef) {
@@ -81,80 +190,53 @@ __global__ void __launch_bounds__(128) jac_kernel(const SimConst sc, const Rollo
     float cph0, sph0;
     yaw_sincos(s0.ph[0], &sph0, &cph0);
     const float j1 = (float)(j + 1), step = dist / (float)sc.T;
+    float row[kRow];
+    pair_row(sc, s, cs[0], sn[0], sl.p0x, sl.p0y, sl.dx, sl.dy, sl.w, j1, step, cph0, sph0, off, row);
+    float4* out = reinterpret_cast<float4*>(coef_row(coef, HT, i, t));
+#pragma unroll
+    for (int v = 0; v < kRow / 4; ++v)
+        out[v] = make_float4(row[4 * v], row[4 * v + 1], row[4 * v + 2], row[4 * v + 3]);
+}
 
-    float J[3][6], eph[3], eoff[3], edist[3], ew[4][3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        eph[m] = eoff[m] = edist[m] = 0.f;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) J[m][q] = 0.f;
+// Bounded wait on an mbarrier phase by a whole warp (false: gave up).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity) {
+    bool ok;
+    unsigned spins = 0;
+    while (!(ok = async::mbar_try_wait(bar, parity)) && ++spins < async::kWaitLimit) {
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {   // choice q pushes side q of the block
-        const float px = sl.p0x[q] + j1 * sl.dx[q], py = sl.p0y[q] + j1 * sl.dy[q];
-        const float vpx = sl.dx[q] * sc.inv_dt, vpy = sl.dy[q] * sc.inv_dt;
-        // pusher start point p0 = pos + R l and displacement -R n dist/T at the action start
-        float nx, ny;
-        side_normal(q, nx, ny);
-        const float tx = -ny, ty = nx;
-        const float lx = nx * (sc.hs + sc.r) + tx * off;
-        const float ly = ny * (sc.hs + sc.r) + ty * off;
-        const float dRl_x = -sph0 * lx - cph0 * ly, dRl_y = cph0 * lx - sph0 * ly;
-        const float dRn_x = -sph0 * nx - cph0 * ny, dRn_y = cph0 * nx - sph0 * ny;
-        const float ux = -(cph0 * nx - sph0 * ny), uy = -(sph0 * nx + cph0 * ny);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            const DiskGrad g = disk_box_vjp(sc, px, py, vpx, vpy, s.x[0], s.y[0], cs[0], sn[0],
-                                            s.vx[0], s.vy[0], s.om[0], sl.w[q], m == 0 ? 1.f : 0.f,
-                                            m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f);
-            J[m][0] += g.bx;
-            J[m][1] += g.by;
-            J[m][2] += g.ph;
-            J[m][3] += g.vx;
-            J[m][4] += g.vy;
-            J[m][5] += g.om;
-            const float adx = j1 * g.px + g.vpx * sc.inv_dt, ady = j1 * g.py + g.vpy * sc.inv_dt;
-            eph[m] += g.px * dRl_x + g.py * dRl_y - (adx * dRn_x + ady * dRn_y) * step;
-            eoff[m] += (cph0 * g.px + sph0 * g.py) * tx + (-sph0 * g.px + cph0 * g.py) * ty;
-            edist[m] += (adx * ux + ady * uy) / (float)sc.T;
-            ew[q][m] = g.w;
-        }
-    }
-    // ground friction -fl v/sqrt(|v|^2+eps_v^2), -fa om/sqrt(om^2+eps_w^2)
-    const float vx = s.vx[0], vy = s.vy[0], om = s.om[0];
-    const float isv = rsqrtf(vx * vx + vy * vy + sc.eps_v2);
-    const float iso = rsqrtf(om * om + sc.eps_w2);
-    const float isv3 = isv * isv * isv;
-    J[0][3] -= sc.fric_lin * (isv - vx * vx * isv3);
-    J[1][3] += sc.fric_lin * vx * vy * isv3;
-    J[0][4] += sc.fric_lin * vx * vy * isv3;
-    J[1][4] -= sc.fric_lin * (isv - vy * vy * isv3);
-    J[2][5] -= sc.fric_ang * sc.eps_w2 * (iso * iso * iso);
+    return __all_sync(0xffffffffu, ok);
+}
 
-    const float cm[3] = {sc.dt * sc.inv_m, sc.dt * sc.inv_m, sc.dt * sc.inv_I};
-    const int grp = i / kGroup, p = i % kGroup;
-    float* out = coef + ((size_t)grp * HT + t) * kCoef * kGroup + p;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) out[(kM + 6 * m + q) * kGroup] = cm[m] * J[m][q];
-        out[(kEph + m) * kGroup] = cm[m] * eph[m];
-        out[(kEoff + m) * kGroup] = cm[m] * eoff[m];
-        out[(kEdist + m) * kGroup] = cm[m] * edist[m];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) out[(kEw + 3 * q + m) * kGroup] = cm[m] * ew[q][m];
-    }
+// One lane's coefficients of one substep in a staged window (row base = the
+// lane's particle): M and the lane's two forms.
+struct Coefs {
+    float4 c0, c1, c2, c3;
+    float2 c4, e0, e1, e2;
+};
+__device__ __forceinline__ Coefs load_coefs(const float* base, int dt, int lane) {
+    const float* c = base + (size_t)dt * kGroup * kRow;
+    Coefs r;
+    r.c0 = *reinterpret_cast<const float4*>(c);
+    r.c1 = *reinterpret_cast<const float4*>(c + 4);
+    r.c2 = *reinterpret_cast<const float4*>(c + 8);
+    r.c3 = *reinterpret_cast<const float4*>(c + 12);
+    r.c4 = *reinterpret_cast<const float2*>(c + 16);
+    const float2* eb = reinterpret_cast<const float2*>(c + kE + 6 * lane);
+    r.e0 = eb[0];
+    r.e1 = eb[1];
+    r.e2 = eb[2];
+    return r;
 }
 
 // The recurrence, backwards over the H*T substeps: one CTA of 8 particles,
 // a team of 4 lanes per particle.  Every lane carries the state adjoint
-// (redundantly); lane l also accumulates choice l's weight form, and lanes
-// 0, 1, 2 the action-start yaw, offset and distance forms.  Window w of the
-// coefficients is copied into buffer w%2 while window w-1 is consumed.
+// (redundantly); lane l also accumulates form l and choice l's weight form.
+// Window w of the coefficients is copied into buffer w%2 while window w-1 is
+// consumed.
 struct ScanSmem {
     uint64_t bar[2];
     float pad[28];   // the buffers start 128 B in
-    float buf[2][kWin * kCoef * kGroup];
+    float buf[2][kWin * kGroup * kRow];
 };
 
 __global__ void __launch_bounds__(32) scan_kernel(const SimConst sc, const RolloutArgs a,
@@ -170,14 +252,14 @@ __global__ void __launch_bounds__(32) scan_kernel(const SimConst sc, const Rollo
     if (!on) i = a.N - 1;   // surplus team: shadows the last particle, writes nothing
     const int T = sc.T, HT = sc.H * sc.T;
     const int nwin = (HT + kWin - 1) / kWin;
-    const float* cgrp = coef + (size_t)grp * HT * kCoef * kGroup;
+    const float* cgrp = coef + (size_t)grp * HT * kGroup * kRow;
     // window w covers substeps [lo(w), hi(w)), counted from the end
     auto lo = [&](int w) { return max(0, HT - (w + 1) * kWin); };
     auto hi = [&](int w) { return HT - w * kWin; };
     auto issue = [&](int w) {
-        const unsigned bytes = (unsigned)((hi(w) - lo(w)) * kCoef * kGroup * sizeof(float));
+        const unsigned bytes = (unsigned)((hi(w) - lo(w)) * kGroup * kRow * sizeof(float));
         async::mbar_expect_tx(&sm.bar[w & 1], bytes);
-        async::tma_load_1d(sm.buf[w & 1], cgrp + (size_t)lo(w) * kCoef * kGroup, bytes,
+        async::tma_load_1d(sm.buf[w & 1], cgrp + (size_t)lo(w) * kGroup * kRow, bytes,
                            &sm.bar[w & 1]);
     };
     if (tid == 0) {
@@ -186,8 +268,8 @@ __global__ void __launch_bounds__(32) scan_kernel(const SimConst sc, const Rollo
         async::fence_async_shared();
     }
     __syncthreads();
-    bool pending[2] = {true, nwin > 1};
-    unsigned parity[2] = {0u, 0u};
+    bool pending0 = true, pending1 = nwin > 1;
+    unsigned parity0 = 0u, parity1 = 0u;
     if (tid == 0) {
         issue(0);
         if (nwin > 1) issue(1);
@@ -202,46 +284,53 @@ __global__ void __launch_bounds__(32) scan_kernel(const SimConst sc, const Rollo
     float aph = 2.f * sc.w_yaw * wrapf(sf.ph[0] - sc.goal[0][2]);
     float avx = 0.f, avy = 0.f, aom = 0.f;
 
-    const int fe = kEph + 3 * (lane < 3 ? lane : 0);   // lane 3 repeats lane 0's form, unused
-    const int fw = kEw + 3 * lane;
     float dX = 0.f, dY = 0.f, e = 0.f, az = 0.f;
     bool bad = false, failed = false;
-    int k = sc.H - 1, j = T - 1;
     const bool hard = a.hard != 0;
+    int k = sc.H - 1;   // the action of the next substep down
     for (int w = 0; w < nwin; ++w) {
         const int b = w & 1;
-        bool ok;
-        unsigned spins = 0;
-        while (!(ok = async::mbar_try_wait(&sm.bar[b], parity[b])) && ++spins < async::kWaitLimit) {
-        }
-        if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }   // the copy stays pending
-        parity[b] ^= 1u;
-        pending[b] = false;
+        if (!warp_wait(&sm.bar[b], b ? parity1 : parity0)) { failed = true; break; }
+        if (b) { parity1 ^= 1u; pending1 = false; } else { parity0 ^= 1u; pending0 = false; }
         const int l0 = lo(w);
-        for (int t = hi(w) - 1; t >= l0; --t) {
-            const float* c = sm.buf[b] + (t - l0) * kCoef * kGroup + p;
-            const float v0 = avx + sc.dt * ax, v1 = avy + sc.dt * ay, v2 = aom + sc.dt * aph;
-            float d[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-                d[q] = c[(kM + q) * kGroup] * v0 + c[(kM + 6 + q) * kGroup] * v1 +
-                       c[(kM + 12 + q) * kGroup] * v2;
-            ax += d[0];
-            ay += d[1];
-            aph += d[2];
-            avx = v0 + d[3];
-            avy = v1 + d[4];
-            aom = v2 + d[5];
-            dX -= d[0];   // the pushers move with the block's start position
-            dY -= d[1];
-            e += c[fe * kGroup] * v0 + c[(fe + 1) * kGroup] * v1 + c[(fe + 2) * kGroup] * v2;
-            az += c[fw * kGroup] * v0 + c[(fw + 1) * kGroup] * v1 + c[(fw + 2) * kGroup] * v2;
-            if (j > 0) { --j; continue; }
+        const float* base = sm.buf[b] + (size_t)p * kRow;
+        int t = hi(w) - 1;
+        while (t >= l0) {
+            // the substeps of this window inside action k, then (if it starts
+            // here) action k's placement and gradient
+            const int a0 = k * T, stop = max(l0, a0);
+            // substep t's coefficients; the next one down is loaded while t is computed
+            Coefs cur = load_coefs(base, t - l0, lane);
+            for (; t >= stop; --t) {
+                const Coefs nxt = load_coefs(base, max(t - 1, stop) - l0, lane);
+                const float4 c0 = cur.c0, c1 = cur.c1, c2 = cur.c2, c3 = cur.c3;
+                const float2 c4 = cur.c4, e0 = cur.e0, e1 = cur.e1, e2 = cur.e2;
+                const float v0 = avx + sc.dt * ax, v1 = avy + sc.dt * ay, v2 = aom + sc.dt * aph;
+                // M rows: F_x = (c0, c1.xy), F_y = (c1.zw, c2), T = (c3, c4)
+                const float d0 = c0.x * v0 + c1.z * v1 + c3.x * v2;
+                const float d1 = c0.y * v0 + c1.w * v1 + c3.y * v2;
+                const float d2 = c0.z * v0 + c2.x * v1 + c3.z * v2;
+                const float d3 = c0.w * v0 + c2.y * v1 + c3.w * v2;
+                const float d4 = c1.x * v0 + c2.z * v1 + c4.x * v2;
+                const float d5 = c1.y * v0 + c2.w * v1 + c4.y * v2;
+                ax += d0;
+                ay += d1;
+                aph += d2;
+                avx = v0 + d3;
+                avy = v1 + d4;
+                aom = v2 + d5;
+                dX -= d0;   // the pushers move with the block's start position
+                dY -= d1;
+                e += e0.x * v0 + e0.y * v1 + e1.x * v2;
+                az += e1.y * v0 + e2.x * v1 + e2.y * v2;
+                cur = nxt;
+            }
+            if (t >= a0) continue;   // the window ended inside the action
             // start of action k: the pushers' placement, then the parameter gradient
-            const int base = tid & ~3;
-            const float dph = __shfl_sync(0xffffffffu, e, base);
-            const float aoff = __shfl_sync(0xffffffffu, e, base + 1);
-            float adist = __shfl_sync(0xffffffffu, e, base + 2);
+            const int tb = tid & ~3;
+            const float dph = __shfl_sync(0xffffffffu, e, tb);
+            const float aoff = __shfl_sync(0xffffffffu, e, tb + 1);
+            float adist = __shfl_sync(0xffffffffu, e, tb + 2);
             ax += dX;
             ay += dY;
             aph += dph;
@@ -267,19 +356,20 @@ __global__ void __launch_bounds__(32) scan_kernel(const SimConst sc, const Rollo
             }
             dX = dY = e = az = 0.f;
             --k;
-            j = T - 1;
         }
         __syncwarp();
         if (w + 2 < nwin) {   // the buffer is free again
             if (tid == 0) issue(w + 2);
-            pending[b] = true;
+            if (b) pending1 = true; else pending0 = true;
         }
     }
     if (failed) {
         if (tid == 0) atomicOr(flag, 2);
-        for (int b = 0; b < 2; ++b)   // let the copies in flight land before the CTA exits
-            for (unsigned s = 0; pending[b] && s < async::kWaitLimit; ++s)
-                if (async::mbar_try_wait(&sm.bar[b], parity[b])) break;
+        // let the copies in flight land before the CTA exits
+        for (unsigned s = 0; pending0 && s < async::kWaitLimit; ++s)
+            if (async::mbar_try_wait(&sm.bar[0], parity0)) break;
+        for (unsigned s = 0; pending1 && s < async::kWaitLimit; ++s)
+            if (async::mbar_try_wait(&sm.bar[1], parity1)) break;
         return;
     }
     // an overflowed reverse sweep gives the particle a zero gradient, and is counted
@@ -297,7 +387,7 @@ constexpr size_t kScanSmem = sizeof(ScanSmem);
 
 size_t adjoint_time_coef_floats(int n, int H, int T) {
     return (size_t)((n + rollout::kGroup - 1) / rollout::kGroup) * rollout::kGroup * H * T *
-           rollout::kCoef;
+           rollout::kRow;
 }
 size_t adjoint_time_rel_floats(int n, int H) { return (size_t)n * H * rollout::kRel; }
 

@@ -38,6 +38,7 @@ constexpr long long kMaxStatsIters = 1 << 20;
 // the time-parallel reverse sweep keeps 39 coefficients per particle and
 // substep; above this it is not set up (the sequential sweep runs)
 constexpr size_t kMaxTimeParallelBytes = (size_t)4 << 30;
+constexpr int kTimeParallelMaxN = 3072;   // the automatic mode's crossover (see time_parallel)
 
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes at;
@@ -69,7 +70,7 @@ struct stamp_problem {
     int fwd_lanes = 0, adj_lanes = 0;
     // one-block reverse sweep as a linear recurrence in time (checkpoint
     // interval 1): its scratch exists when the problem qualifies
-    int adj_mode = STAMP_ADJ_TIME_PARALLEL;
+    int adj_mode = STAMP_ADJ_AUTO;
     float *pit_rel = nullptr, *pit_coef = nullptr;
     bool pit_ok = false;
     // the bandwidth (pairwise distances + median) depends on theta only: the
@@ -163,6 +164,17 @@ stamp_status check_dev(const void* ptr, const char* name, bool allow_null = fals
         if (s_ != STAMP_OK) return s_;    \
     } while (0)
 
+// The reverse sweep a call with N particles uses: time-parallel where its
+// scratch exists and, in the automatic mode, up to kTimeParallelMaxN
+// particles -- measured on GB300 (one block, H = 4, T = 100): the
+// time-parallel sweep takes half the sequential one's time at 1024
+// particles and breaks even near 4096, where the sequential teams fill the
+// GPU and the Jacobians' extra arithmetic no longer comes for free.
+bool time_parallel(const stamp_problem* p, int N) {
+    if (!p->pit_ok || p->adj_mode == STAMP_ADJ_SEQUENTIAL) return false;
+    return p->adj_mode == STAMP_ADJ_TIME_PARALLEL || N <= kTimeParallelMaxN;
+}
+
 stamp_status fwd(stamp_problem* p, const float* theta, int N, unsigned long long seed, int iter,
                  int hard, float* cost, float* final_state, unsigned* stats_word,
                  const float* init_states = nullptr) {
@@ -183,7 +195,7 @@ stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
     stamp::RolloutArgs a{};
     a.theta = theta; a.N = N; a.seed = p->last_seed; a.iter = p->last_iter; a.hard = p->last_hard;
     a.tape = p->tape; a.grad = grad; a.dropped = p->dropped;
-    if (p->adj_mode == STAMP_ADJ_TIME_PARALLEL && p->pit_ok)
+    if (time_parallel(p, N))
         return timed(p, STAMP_K_ROLLOUT_ADJ, [&] {
             return stamp::launch_adjoint_time(p->sc, a, p->pit_rel, p->pit_coef, p->flag, p->stream);
         });
@@ -693,16 +705,16 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
 
 stamp_status stamp_set_adjoint_mode(stamp_problem* p, int mode) {
     if (!p) return fail(STAMP_EINVAL, "NULL problem");
-    if (mode != STAMP_ADJ_SEQUENTIAL && mode != STAMP_ADJ_TIME_PARALLEL)
-        return fail(STAMP_EINVAL, "adjoint mode must be STAMP_ADJ_SEQUENTIAL or STAMP_ADJ_TIME_PARALLEL");
+    if (mode != STAMP_ADJ_SEQUENTIAL && mode != STAMP_ADJ_TIME_PARALLEL && mode != STAMP_ADJ_AUTO)
+        return fail(STAMP_EINVAL, "unknown adjoint mode %d", mode);
     p->adj_mode = mode;
     return STAMP_OK;
 }
 
-stamp_status stamp_get_adjoint_mode(stamp_problem* p, int* mode) {
+stamp_status stamp_get_adjoint_mode(stamp_problem* p, int N, int* mode) {
     if (!p || !mode) return fail(STAMP_EINVAL, "NULL problem or mode");
-    *mode = (p->adj_mode == STAMP_ADJ_TIME_PARALLEL && p->pit_ok) ? STAMP_ADJ_TIME_PARALLEL
-                                                                  : STAMP_ADJ_SEQUENTIAL;
+    STAMP_TRY(check_n(p, N));
+    *mode = time_parallel(p, N) ? STAMP_ADJ_TIME_PARALLEL : STAMP_ADJ_SEQUENTIAL;
     return STAMP_OK;
 }
 

@@ -21,7 +21,7 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 STAMP_OK, STAMP_EINVAL, STAMP_ENOMEM, STAMP_ECUDA, STAMP_ENONFINITE, STAMP_ETIMEOUT = range(6)
-STAMP_ADJ_SEQUENTIAL, STAMP_ADJ_TIME_PARALLEL = 0, 1
+STAMP_ADJ_SEQUENTIAL, STAMP_ADJ_TIME_PARALLEL, STAMP_ADJ_AUTO = 0, 1, 2
 KERNELS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init",
            "surrogate", "screen")
 STAMP_NKERNELS = len(KERNELS)
@@ -68,7 +68,7 @@ _sigs = {
     "stamp_set_lanes": [_vp, _i, _i],
     "stamp_set_overlap": [_vp, _i],
     "stamp_set_adjoint_mode": [_vp, _i],
-    "stamp_get_adjoint_mode": [_vp, _vp],
+    "stamp_get_adjoint_mode": [_vp, _i, _vp],
     "stamp_dropped_gradients": [_vp, _vp],
     "stamp_svgd_step_noalloc": [_vp, _vp, _i, _i, _vp, _vp, _i, _f, _i, _vp, _vp, _vp],
     "stamp_mlp_create": [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)],
@@ -308,13 +308,13 @@ class Problem:
         _check(_lib.stamp_set_overlap(self.handle, int(enable)))
 
     def set_adjoint_mode(self, mode):
-        """STAMP_ADJ_TIME_PARALLEL (default where it applies) or STAMP_ADJ_SEQUENTIAL."""
+        """STAMP_ADJ_AUTO (default), STAMP_ADJ_TIME_PARALLEL or STAMP_ADJ_SEQUENTIAL."""
         _check(_lib.stamp_set_adjoint_mode(self.handle, int(mode)))
 
-    def adjoint_mode(self):
-        """The reverse sweep the problem's adjoints use."""
+    def adjoint_mode(self, N):
+        """The reverse sweep a call with N particles uses."""
         m = ctypes.c_int()
-        _check(_lib.stamp_get_adjoint_mode(self.handle, ctypes.byref(m)))
+        _check(_lib.stamp_get_adjoint_mode(self.handle, int(N), ctypes.byref(m)))
         return m.value
 
     def set_lanes(self, fwd_lanes, adj_lanes):

@@ -208,7 +208,7 @@ def test_hard_rollout_time_parallel_gradient_has_no_logit_term():
     P, init, goal, M, D, theta = setup("pusher1_h2", dict(SOFT, ckpt_every=1), N, seed)
     from paper_2310_01775_gb300 import stamp as S
     prob = S.Problem(P, init, goal, N, torch.cuda.current_stream().cuda_stream)
-    assert prob.adjoint_mode() == S.STAMP_ADJ_TIME_PARALLEL
+    assert prob.adjoint_mode(N) == S.STAMP_ADJ_TIME_PARALLEL
     th = torch.tensor(theta, device="cuda")
     c = torch.empty(N, device="cuda")
     g = torch.empty(N, D, device="cuda")
@@ -233,9 +233,30 @@ def test_adjoint_mode_where_it_applies():
         P = W.params(name, **over)
         init, goal = W.scene(P, 0)
         prob = S.Problem(P, init, goal, 8, torch.cuda.current_stream().cuda_stream)
-        assert prob.adjoint_mode() == want, (name, over)
+        assert prob.adjoint_mode(8) == want, (name, over)
         prob.set_adjoint_mode(S.STAMP_ADJ_SEQUENTIAL)
-        assert prob.adjoint_mode() == S.STAMP_ADJ_SEQUENTIAL
+        assert prob.adjoint_mode(8) == S.STAMP_ADJ_SEQUENTIAL
         with pytest.raises(S.StampError):
             prob.set_adjoint_mode(7)
         prob.close()
+    # the automatic mode leaves a launch that would not fit on the GPU at once
+    # to the sequential sweep
+    P = W.params("pusher1_h4")
+    init, goal = W.scene(P, 0)
+    prob = S.Problem(P, init, goal, 16384, torch.cuda.current_stream().cuda_stream)
+    assert prob.adjoint_mode(1024) == S.STAMP_ADJ_TIME_PARALLEL
+    assert prob.adjoint_mode(16384) == S.STAMP_ADJ_SEQUENTIAL
+    prob.set_adjoint_mode(S.STAMP_ADJ_TIME_PARALLEL)
+    assert prob.adjoint_mode(16384) == S.STAMP_ADJ_TIME_PARALLEL
+    prob.close()
+
+
+@pytest.mark.parametrize("lanes", [4, 2])
+def test_time_parallel_sweep_after_either_forward_team_width(lanes):
+    """The time-parallel sweep reads only the tape and the relaxed parameters,
+    so it serves a forward of any team width; both against the oracle."""
+    seed, it, N = 5, 2, 45
+    P, init, goal, M, D, theta = setup("pusher1_h4", dict(SOFT, H=2), N, seed)
+    cost, fin, tape, grad = gpu_rollout(P, init, goal, theta, seed, it, lanes, adj_mode=1)
+    gum = O.gumbel_noise(seed, it, N, P["H"], M)
+    Reference(theta, P, init, goal, gum, C=1).check(tape, fin, cost, grad, min_frac=0.9)
