@@ -40,7 +40,8 @@ SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes, 1 FMA = 2
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture (profiles/rollout_pusher1_h4.md), valid while the kernel source is
 # unchanged (sha256 prefix of csrc/rollout.cuh at capture time).
-TRAFFIC = {("pusher1_h4", "rollout_adj"): ("b0b4b89f0df5d44d", 9.998592e6)}
+TRAFFIC = {("pusher1_h4", "rollout_adj"): ("b0b4b89f0df5d44d", 9.998592e6),
+           ("pusher1_h4", "rollout_fwd"): ("b0b4b89f0df5d44d", 1.23904e5)}
 
 
 def peaks():
@@ -337,6 +338,10 @@ def main():
         R.finish()
         return
 
+    # kernels per recorded launch: the time-parallel reverse sweep is three
+    # (relaxed parameters, Jacobians, recurrence)
+    per_rec = {"rollout_adj": 3 if prob.adjoint_mode(N) == S.STAMP_ADJ_TIME_PARALLEL else 1}
+    gpu_launches = int(sum(n * per_rec.get(k, 1) for k, (_, n) in kt_all.items())) * args.steps
     # roofline of the dominant kernel (FP32 ALU bound; FLOPs from the oracle count)
     mhz, hbm, src = peaks()
     peak_tflops = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -376,7 +381,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args, P), "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e,
-            "gpu_launches": int(sum(n for _, n in kt_all.values())) * args.steps,
+            "gpu_launches": gpu_launches,
             "kernels_ms_one_step": {k: round(v[0], 3) for k, v in kt_all.items() if v[1]},
             "surrogate_vs_plain": sur, "batched_serving": bat, "solver_variants": var}
     print(json.dumps(line), flush=True)
