@@ -49,12 +49,164 @@ struct ItemJac {
     float eph[3], eoff[3], edist[3], ew[3];
 };
 
+// disk_box's forward quantities (unweighted force), as disk_box_vjp forms
+// them; active = the pusher touches the block with a compressive force.
+struct DiskFwd {
+    float dx, dy, qx, qy, sx, sy, mx, my, il, nlx, nly;
+    float nx, ny, rx, ry, wx, wy, vn, fn, tx, ty, iden, gt, fx, fy;
+    bool outside, xa, active;
+};
+
+__device__ __forceinline__ DiskFwd disk_fwd(const SimConst& sc, float px, float py, float vpx,
+                                            float vpy, float bx, float by, float cph, float sph,
+                                            float vx, float vy, float om) {
+    DiskFwd f;
+    f.active = false;
+    f.dx = px - bx;
+    f.dy = py - by;
+    const float lx = cph * f.dx + sph * f.dy, ly = -sph * f.dx + cph * f.dy;
+    f.qx = fabsf(lx) - sc.hs;
+    f.qy = fabsf(ly) - sc.hs;
+    f.sx = lx >= 0.f ? 1.f : -1.f;
+    f.sy = ly >= 0.f ? 1.f : -1.f;
+    f.outside = f.qx > 0.f || f.qy > 0.f;
+    f.xa = f.qx >= f.qy;
+    f.mx = fmaxf(f.qx, 0.f);
+    f.my = fmaxf(f.qy, 0.f);
+    f.il = rsqrtf(fmaxf(f.mx * f.mx + f.my * f.my, 1e-30f));
+    const float ln = (f.mx * f.mx + f.my * f.my) * f.il;
+    const float sd = f.outside ? ln : fmaxf(f.qx, f.qy);
+    f.nlx = f.outside ? f.sx * f.mx * f.il : (f.xa ? f.sx : 0.f);
+    f.nly = f.outside ? f.sy * f.my * f.il : (f.xa ? 0.f : f.sy);
+    const float delta = sc.r - sd;
+    if (!(delta > 0.f)) return f;
+    f.nx = cph * f.nlx - sph * f.nly;
+    f.ny = sph * f.nlx + cph * f.nly;
+    f.rx = px - sc.r * f.nx - bx;
+    f.ry = py - sc.r * f.ny - by;
+    f.wx = vpx - (vx - om * f.ry);
+    f.wy = vpy - (vy + om * f.rx);
+    f.vn = f.wx * f.nx + f.wy * f.ny;
+    f.fn = sc.k * delta - sc.c * f.vn;
+    if (!(f.fn > 0.f)) return f;
+    f.tx = f.wx - f.vn * f.nx;
+    f.ty = f.wy - f.vn * f.ny;
+    f.iden = rsqrtf(f.tx * f.tx + f.ty * f.ty + sc.eps_t2);
+    f.gt = sc.mu_c * f.fn * f.iden;
+    f.fx = -f.fn * f.nx + f.gt * f.tx;
+    f.fy = -f.fn * f.ny + f.gt * f.ty;
+    f.active = true;
+    return f;
+}
+
+// Adjoints of the pusher position and velocity, the block yaw and spin, for
+// the adjoint (afx, afy) of the weighted contact force and (arx, ary) of the
+// lever arm r = x_c - b (the torque's part) -- disk_box_vjp's reverse pass.
+// The block position and velocity get the negated pusher ones.
+struct DiskAdj {
+    float px, py, vpx, vpy, ph, om;
+};
+// The reverse pass through the normal n = R nl and the penetration depth,
+// from the adjoints (anx, any) of n and asd of the signed distance.
+__device__ __forceinline__ DiskAdj disk_bwd_geometry(const DiskFwd& f, float cph, float sph,
+                                                     float anx, float any, float asd, DiskAdj g) {
+    const float anlx = cph * anx + sph * any;
+    const float anly = -sph * anx + cph * any;
+    float acph = anx * f.nlx + any * f.nly;
+    float asph = -anx * f.nly + any * f.nlx;
+    // outside: through the normalised clamped offset; inside: the chosen axis
+    const float aln = asd - (anlx * f.nlx + anly * f.nly) * f.il;
+    const float amx = (f.sx * anlx + aln * f.mx) * f.il, amy = (f.sy * anly + aln * f.my) * f.il;
+    const float aqx = f.outside ? (f.qx > 0.f ? amx : 0.f) : (f.xa ? asd : 0.f);
+    const float aqy = f.outside ? (f.qy > 0.f ? amy : 0.f) : (f.xa ? 0.f : asd);
+    const float alx = aqx * f.sx, aly = aqy * f.sy;
+    const float adx = cph * alx - sph * aly, ady = sph * alx + cph * aly;
+    acph += alx * f.dx + aly * f.dy;
+    asph += alx * f.dy - aly * f.dx;
+    g.px += adx;
+    g.py += ady;
+    g.ph = -sph * acph + cph * asph;
+    return g;
+}
+
+__device__ __forceinline__ DiskAdj disk_bwd(const SimConst& sc, const DiskFwd& f, float cph,
+                                            float sph, float om, float afx, float afy, float arx,
+                                            float ary) {
+    DiskAdj g;
+    // f = -fn n + gt t
+    float afn = -(afx * f.nx + afy * f.ny);
+    float anx = -afx * f.fn, any = -afy * f.fn;
+    const float agt = afx * f.tx + afy * f.ty;
+    float atx = afx * f.gt, aty = afy * f.gt;
+    // gt = mu_c fn / den, den = sqrt(|t|^2 + eps^2)
+    afn += agt * sc.mu_c * f.iden;
+    const float aden = -agt * f.gt * f.iden;
+    atx += aden * f.tx * f.iden;
+    aty += aden * f.ty * f.iden;
+    // t = w - vn n
+    float awx = atx, awy = aty;
+    float avn = -(atx * f.nx + aty * f.ny);
+    anx -= atx * f.vn;
+    any -= aty * f.vn;
+    // fn = k delta - c vn
+    const float adelta = sc.k * afn;
+    avn -= sc.c * afn;
+    // vn = w . n
+    awx += avn * f.nx;
+    awy += avn * f.ny;
+    anx += avn * f.wx;
+    any += avn * f.wy;
+    // w = vp - v - om x r
+    g.vpx = awx;
+    g.vpy = awy;
+    g.om = awx * f.ry - awy * f.rx;
+    ary += awx * om;
+    arx -= awy * om;
+    // r = p - r_p n - b
+    g.px = arx;
+    g.py = ary;
+    anx -= sc.r * arx;
+    any -= sc.r * ary;
+    return disk_bwd_geometry(f, cph, sph, anx, any, -adelta, g);
+}
 __device__ __forceinline__ void item_jac(const SimConst& sc, const Blocks<1>& s, float cs, float sn,
                                          int q, float p0x, float p0y, float dxq, float dyq,
                                          float w, float j1, float step, float cph0, float sph0,
                                          float off, ItemJac& o) {
     const float px = p0x + j1 * dxq, py = p0y + j1 * dyq;
     const float vpx = dxq * sc.inv_dt, vpy = dyq * sc.inv_dt;
+    const DiskFwd f = disk_fwd(sc, px, py, vpx, vpy, s.x[0], s.y[0], cs, sn, s.vx[0], s.vy[0],
+                               s.om[0]);
+    if (!f.active) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) o.J[m][c] = 0.f;
+            o.eph[m] = o.eoff[m] = o.edist[m] = o.ew[m] = 0.f;
+        }
+        return;
+    }
+    // rows F_x, F_y: unit force adjoints; row T: the torque r x f adjoint is
+    // (-ry, rx) on the force plus (w fy, -w fx) on the lever arm, and the
+    // reverse pass is linear -- so row T = -ry row F_x + rx row F_y + the
+    // lever-arm-only pass
+    DiskAdj g[3];
+    g[0] = disk_bwd(sc, f, cs, sn, s.om[0], w, 0.f, 0.f, 0.f);
+    g[1] = disk_bwd(sc, f, cs, sn, s.om[0], 0.f, w, 0.f, 0.f);
+    {
+        DiskAdj r;
+        r.px = w * f.fy;
+        r.py = -w * f.fx;
+        r.vpx = r.vpy = r.om = 0.f;
+        r = disk_bwd_geometry(f, cs, sn, -sc.r * r.px, -sc.r * r.py, 0.f, r);
+        g[2].px = -f.ry * g[0].px + f.rx * g[1].px + r.px;
+        g[2].py = -f.ry * g[0].py + f.rx * g[1].py + r.py;
+        g[2].vpx = -f.ry * g[0].vpx + f.rx * g[1].vpx;
+        g[2].vpy = -f.ry * g[0].vpy + f.rx * g[1].vpy;
+        g[2].ph = -f.ry * g[0].ph + f.rx * g[1].ph + r.ph;
+        g[2].om = -f.ry * g[0].om + f.rx * g[1].om;
+    }
+    const float gw[3] = {f.fx, f.fy, f.rx * f.fy - f.ry * f.fx};   // unweighted force, torque
     // pusher start point p0 = pos + R l and displacement -R n dist/T at the action start
     float nx, ny;
     side_normal(q, nx, ny);
@@ -66,20 +218,18 @@ __device__ __forceinline__ void item_jac(const SimConst& sc, const Blocks<1>& s,
     const float ux = -(cph0 * nx - sph0 * ny), uy = -(sph0 * nx + cph0 * ny);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const DiskGrad g = disk_box_vjp(sc, px, py, vpx, vpy, s.x[0], s.y[0], cs, sn, s.vx[0],
-                                        s.vy[0], s.om[0], w, m == 0 ? 1.f : 0.f,
-                                        m == 1 ? 1.f : 0.f, m == 2 ? 1.f : 0.f);
-        o.J[m][0] = g.bx;
-        o.J[m][1] = g.by;
-        o.J[m][2] = g.ph;
-        o.J[m][3] = g.vx;
-        o.J[m][4] = g.vy;
-        o.J[m][5] = g.om;
-        const float adx = j1 * g.px + g.vpx * sc.inv_dt, ady = j1 * g.py + g.vpy * sc.inv_dt;
-        o.eph[m] = g.px * dRl_x + g.py * dRl_y - (adx * dRn_x + ady * dRn_y) * step;
-        o.eoff[m] = (cph0 * g.px + sph0 * g.py) * tx + (-sph0 * g.px + cph0 * g.py) * ty;
+        o.J[m][0] = -g[m].px;   // the block position enters as -p
+        o.J[m][1] = -g[m].py;
+        o.J[m][2] = g[m].ph;
+        o.J[m][3] = -g[m].vpx;  // the block velocity enters as -vp
+        o.J[m][4] = -g[m].vpy;
+        o.J[m][5] = g[m].om;
+        const float adx = j1 * g[m].px + g[m].vpx * sc.inv_dt;
+        const float ady = j1 * g[m].py + g[m].vpy * sc.inv_dt;
+        o.eph[m] = g[m].px * dRl_x + g[m].py * dRl_y - (adx * dRn_x + ady * dRn_y) * step;
+        o.eoff[m] = (cph0 * g[m].px + sph0 * g[m].py) * tx + (-sph0 * g[m].px + cph0 * g[m].py) * ty;
         o.edist[m] = (adx * ux + ady * uy) / (float)sc.T;
-        o.ew[m] = g.w;
+        o.ew[m] = gw[m];
     }
 }
 
