@@ -19,9 +19,10 @@
 // per substep (scan_kernel, its coefficients streamed into shared memory by
 // TMA bulk copies a window ahead).
 //
-// The contact Jacobian comes from disk_box_vjp with unit seeds -- the
-// function the sequential sweep differentiates with -- so both sweeps take
-// the same derivatives and differ only in summation order.
+// The contact Jacobian takes disk_box_vjp's forward and reverse passes (the
+// sequential sweep's derivative of the contact) once forward and twice in
+// reverse per pusher -- the force rows -- and the torque row by linearity,
+// so both sweeps take the same derivatives and differ only in rounding.
 #include "async_copy.cuh"
 #include "rollout.cuh"
 
