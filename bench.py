@@ -379,7 +379,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, P), "roofline": roof, "cpu_baseline": cpu,
+            "config": dict(workload_config(args, P),
+                           reverse_sweep="time-parallel" if per_rec["rollout_adj"] == 3 else "sequential"),
+            "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": gpu_launches,
             "kernels_ms_one_step": {k: round(v[0], 3) for k, v in kt_all.items() if v[1]},
