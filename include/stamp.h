@@ -178,7 +178,7 @@ stamp_status stamp_sync(stamp_problem* prob);
  * totals are gathered at stamp_sync / stamp_solve.  Kernel ids: */
 enum {
     STAMP_K_ROLLOUT_FWD = 0,  /* forward rollout (relaxed or hard) */
-    STAMP_K_ROLLOUT_ADJ = 1,  /* checkpointed adjoint */
+    STAMP_K_ROLLOUT_ADJ = 1,  /* reverse sweep (time-parallel: its three launches together) */
     STAMP_K_PAIRWISE = 2,     /* pairwise distances + first median digit */
     STAMP_K_MEDIAN = 3,       /* remaining median digits */
     STAMP_K_PHI = 4,          /* Stein direction */
