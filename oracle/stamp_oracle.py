@@ -45,9 +45,14 @@ Readings where the paper is silent (it delegates physics to its simulator):
     N = 1 or h < 1e-12;
   * Gumbel noise from SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a
     counter-based generator; see ``sm64``.
-Parity status: every function here is pinned by a test in tests/test_oracle_*.py
-except whole multi-iteration solves, whose per-particle values are chaotic
-(parity unpinned for those values; only the final plan set is compared).
+Parity status: every function here is pinned by a test in tests/test_oracle_*.py.
+``solve`` (Algorithm 1 over many iterations) is pinned by brute force
+(tests/test_oracle_solve_modes.py): on planted two-push problems with the
+softer contact, its final particles hold every side sequence that a grid
+search plus gradient polish shows can reach cost < 1e-2, move downhill, keep
+spreading, and end on such a mode; a sign error in the gradient and a dropped
+repulsion term each fail that pin.  Per-particle values of long solves at the
+stiff contact constants are chaotic and stay unpinned.
 """
 from __future__ import annotations
 
