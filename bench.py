@@ -36,12 +36,12 @@ UNIT = "particle-substeps/s"
 # oracle's own operations (oracle/flops.py): forward, reverse sweep.
 FLOPS_PER_UNIT = {1: (447.2, 863.2), 2: (2544.4, 5005.0), 3: (6293.5, 12860.9),
                   4: (11694.7, 24711.2)}
-SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes, 1 FMA = 2 FLOP
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture (profiles/rollout_pusher1_h4.md), valid while the kernel source is
-# unchanged (sha256 prefix of csrc/rollout.cuh at capture time).
-TRAFFIC = {("pusher1_h4", "rollout_adj"): ("b0b4b89f0df5d44d", 9.998592e6),
-           ("pusher1_h4", "rollout_fwd"): ("b0b4b89f0df5d44d", 1.23904e5)}
+FP32_LANES = 128                    # FP32 lanes per SM; 1 FMA = 2 FLOP
+# DRAM bytes (read + write) per launch of a rollout kernel, from one ncu
+# capture of the workload, valid while the kernel sources are unchanged
+# (sha256 prefix over the rollout sources at capture time).
+TRAFFIC = {}
+ROLLOUT_SOURCES = ("rollout.cuh", "adjoint_time.cu", "adjoint_replay.cu")
 
 
 def peaks():
@@ -51,6 +51,25 @@ def peaks():
             d = json.load(f)
         return d.get("sm_max_mhz", 2070.0), d.get("hbm_gbs", 6775.6), "measured"
     return 2070.0, 6800.0, "fallback"
+
+
+def rollout_source_hash():
+    h = hashlib.sha256()
+    for name in ROLLOUT_SOURCES:
+        path = os.path.join(ROOT, "paper_2310_01775_gb300", "csrc", name)
+        if os.path.exists(path):
+            h.update(open(path, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def fp32_peak(local):
+    """Measured FP32 FMA roof (the library's microbenchmark) with the SM
+    clocks sampled while it runs."""
+    from paper_2310_01775_gb300 import stamp as S
+    clk = Clocks(local)
+    tflops, ms = S.stamp_fp32_fma_peak(40)
+    c = clk.stop()
+    return tflops, ms, c
 
 
 class Clocks:
@@ -86,11 +105,14 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_sample(P, init, goal, seed, n_particles, iters=1):
+def cpu_oracle_sample(P, init, goal, seed, n_particles, iters=1, actions=None):
     """Time the FP64 oracle on a bounded sample: n_particles of the workload,
-    `iters` iterations of rollout + reverse sweep + Stein step."""
+    `iters` iterations of rollout + reverse sweep + Stein step over the first
+    `actions` pushes of the plan (all H by default)."""
     import torch
     from oracle import stamp_oracle as O
+    if actions:
+        P = dict(P, H=min(actions, P["H"]))
     M, _, D = O.dims(P)
     th = O.init_theta(seed, n_particles, D)
     m = np.zeros_like(th)
@@ -110,17 +132,18 @@ def run_reference(args, P, world, rank):
     if rank != 0:
         return
     init, goal = __import__("paper_2310_01775_gb300.workloads", fromlist=["W"]).scene(P, args.seed)
-    n = args.ref_particles
+    n, acts = args.ref_particles, min(args.ref_actions, P["H"])
     for _ in range(args.warmup):
-        cpu_oracle_sample(P, init, goal, args.seed, max(2, n // 8))
+        cpu_oracle_sample(P, init, goal, args.seed, max(2, n // 8), actions=1)
     times, vals = [], []
     for s in range(args.steps):
-        v, dt, cores = cpu_oracle_sample(P, init, goal, args.seed + s, n)
+        v, dt, cores = cpu_oracle_sample(P, init, goal, args.seed + s, n, actions=acts)
         times.append(dt)
         vals.append(v)
-    units = n * P["H"] * P["T"]
+    units = n * acts * P["T"]
     value = units * len(times) / sum(times)
-    sample = f"{n} of {P['N']} particles, 1 iteration per step"
+    sample = (f"{n} of {P['N']} particles, the first {acts} of {P['H']} pushes "
+              f"({acts * P['T']} substeps), 1 iteration per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
@@ -174,7 +197,7 @@ def surrogate_vs_plain(stream, seeds=(3, 4, 5)):
             "time_to_plain_final_cost": match}
 
 
-def batched_serving(stream, n=256, iters=500, target=1e-3, check_every=10):
+def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3, check_every=10):
     """256 seeded uneven instances (1-4 blocks, H 2-8, N log-uniform 64-1024,
     T=100; goals planted: the end poses of a hard rollout of a random plan)
     solved together: autotuned launch configuration, graph-replayed
@@ -208,8 +231,7 @@ def batched_serving(stream, n=256, iters=500, target=1e-3, check_every=10):
     # block count (forward + reverse) over the units each instance ran
     flops = sum(int(r["iterations"][g]) * d["N"] * d["H"] * 100 * sum(FLOPS_PER_UNIT[d["n_blocks"]])
                 for g, d in enumerate(insts))
-    mhz, _, src = peaks()
-    peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    peak = peak_tflops
     ach = flops / r["seconds"] / 1e12
     done = np.where(stopped, r["seconds_to_target"], r["seconds"])
     b.close()
@@ -226,7 +248,7 @@ def batched_serving(stream, n=256, iters=500, target=1e-3, check_every=10):
             "median_iterations": float(np.median(r["iterations"])),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "over": "the whole solve (all kernels, checks included)",
-                         "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz ({src})"}}
+                         "peak_source": peak_src}}
 
 
 def workload_config(args, P):
@@ -238,15 +260,58 @@ def workload_config(args, P):
             "units_per_step": P["N"] * P["H"] * P["T"] * iters}
 
 
+def time_solves(prob, P, N, seed, steps, warmup, flush, stream):
+    """Per-step device times (ms) of `steps` solves after `warmup` untimed
+    ones; CUDA events on the problem's stream, L2 flushed between steps."""
+    import torch
+    iters = P["svgd_iters"]
+    th = torch.empty(N, prob.D, device="cuda")
+    cost = torch.empty(N, device="cuda")
+    topk = np.zeros(3, dtype=np.int32)
+    for s in range(warmup):
+        prob.solve(N, iters, 0, seed + s, P["lr"], None, th, cost, 3, topk, None)
+    evs = []
+    for s in range(steps):
+        flush.fill_(float(s))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        prob.solve(N, iters, 0, seed + warmup + s, P["lr"], None, th, cost, 3, topk, None)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def secondary_workload(name, seed, flush, stream, steps=5, warmup=3):
+    """The same measurement on another workload (fewer steps), for context."""
+    from paper_2310_01775_gb300 import stamp as S
+    from paper_2310_01775_gb300 import workloads as W
+    P = W.params(name)
+    init, goal = W.scene(P, seed)
+    prob = S.Problem(P, init, goal, P["N"], stream.cuda_stream)
+    ms = time_solves(prob, P, P["N"], seed, steps, warmup, flush, stream)
+    units = P["N"] * P["H"] * P["T"] * P["svgd_iters"]
+    mode = "time-parallel" if prob.adjoint_mode(P["N"]) == S.STAMP_ADJ_TIME_PARALLEL else "sequential"
+    prob.close()
+    return {"workload": f"{name}: {P['n_blocks']} block(s), H={P['H']}, T={P['T']}, N={P['N']}, "
+                        f"C={P['ckpt_every']}, {P['svgd_iters']} SVGD iterations per step",
+            "value": units * steps / (sum(ms) / 1e3), "unit": UNIT, "steps": steps,
+            "ms_per_step": sum(ms) / steps, "reverse_sweep": mode}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="pusher1_h4")
+    ap.add_argument("--workload", default="pusher3_h6")
+    ap.add_argument("--secondary", default="pusher1_h4",
+                    help="a second workload measured with fewer steps ('' to skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-particles", type=int, default=32)
+    ap.add_argument("--ref-actions", type=int, default=1,
+                    help="pushes of the plan in each reference-arm sample")
     ap.add_argument("--baseline-particles", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, nargs=2, default=None)
@@ -290,16 +355,16 @@ def main():
 
     for s in range(args.warmup):
         step(s)
-    # one more (untimed) step with events around every launch: the per-kernel
+    # one untimed step with events around every launch: the per-kernel
     # breakdown and the dominant kernel
     prob.set_profiling(True)
     step(args.warmup)
     torch.cuda.synchronize()
     kt_all = prob.kernel_times()
+    prob.set_profiling(False)
     dom = max(kt_all, key=lambda k: kt_all[k][0])
-    # timed region: per-step CUDA events on the problem's stream, L2 flushed in
-    # between; inside it, events around the dominant kernel's launches only
-    prob.set_profiling_kernels([dom])
+    # timed region: per-step CUDA events on the problem's stream, L2 flushed
+    # in between, no events inside the solves
     R.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
@@ -308,17 +373,23 @@ def main():
         flush.fill_(float(s))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step(args.warmup + s)
+        step(args.warmup + 1 + s)
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    kt = prob.kernel_times()
-    prob.set_profiling(False)
     ms_max = R.max_over_ranks(ms, device=dev)
     R.barrier()
     value = R.throughput(units * args.steps, world, ms_max)
+    # the dominant kernel's launch time: one more step of the same solve with
+    # events around that kernel's launches only
+    prob.set_profiling_kernels([dom])
+    flush.fill_(-1.0)
+    step(args.warmup + 1 + args.steps)
+    torch.cuda.synchronize()
+    kt = prob.kernel_times()
+    prob.set_profiling(False)
 
     # end to end through the public call with host buffers (pinned)
     th_h = torch.empty(N, D, pin_memory=True)
@@ -338,40 +409,41 @@ def main():
         R.finish()
         return
 
-    # kernels per recorded launch: the time-parallel reverse sweep is three
-    # (relaxed parameters, Jacobians, recurrence)
-    per_rec = {"rollout_adj": 3 if prob.adjoint_mode(N) == S.STAMP_ADJ_TIME_PARALLEL else 1}
+    # kernels per recorded launch of the reverse sweep
+    adj_mode = prob.adjoint_mode(N)
+    per_rec = {"rollout_adj": prob.adjoint_launches(N)}
     gpu_launches = int(sum(n * per_rec.get(k, 1) for k, (_, n) in kt_all.items())) * args.steps
-    # roofline of the dominant kernel (FP32 ALU bound; FLOPs from the oracle count)
-    mhz, hbm, src = peaks()
-    peak_tflops = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    # roofline of the dominant kernel: FP32-ALU bound, FLOPs from the oracle's
+    # count, against the measured FMA roof
+    peak_tflops, peak_ms, peak_clocks = fp32_peak(local)
+    peak_src = (f"measured: independent fmaf chains on every SM, {peak_ms:.3f} ms per launch, "
+                f"SM clock {peak_clocks['sm_mhz'] if peak_clocks else 'unsampled'} MHz")
     fpu = FLOPS_PER_UNIT.get(P["n_blocks"])
     roof = None
     if fpu and dom in ("rollout_fwd", "rollout_adj") and kt[dom][1]:
         per_launch_ms = kt[dom][0] / kt[dom][1]
-        # the hard evaluation is also a forward launch: weight by the relaxed ones
         flops = (fpu[0] if dom == "rollout_fwd" else fpu[1]) * N * H * T
         ach = flops / (per_launch_ms / 1e3) / 1e12
-        traffic = None
-        src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2310_01775_gb300", "csrc",
-                                                    "rollout.cuh"), "rb").read()).hexdigest()[:16]
         rec = TRAFFIC.get((args.workload, dom))
-        if rec and rec[0] == src_hash:
-            traffic = rec[1]
+        traffic = rec[1] if rec and rec[0] == rollout_source_hash() else None
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": ach / peak_tflops, "traffic": traffic,
-                "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz ({src})",
-                "ms_per_launch": per_launch_ms}
+                "peak_source": peak_src, "ms_per_launch": per_launch_ms,
+                "flop_per_unit": fpu[0] if dom == "rollout_fwd" else fpu[1],
+                "units_per_launch": N * H * T,
+                "share_of_step": kt_all[dom][0] / sum(v[0] for v in kt_all.values())}
     cpu = None
     if not args.no_cpu_baseline:
         v, dt, cores = cpu_oracle_sample(P, init, goal, seed, args.baseline_particles)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.baseline_particles} of {N} particles, 1 iteration ({dt:.1f} s)"}
+               "sample": f"{args.baseline_particles} of {N} particles, all {H} pushes, "
+                         f"1 iteration ({dt:.1f} s)"}
+    sec = secondary_workload(args.secondary, seed, flush, stream) if args.secondary else None
     sur = bat = None
     if world == 1 and not args.no_surrogate:
         sur = surrogate_vs_plain(stream.cuda_stream)
     if world == 1 and not args.no_batched:
-        bat = batched_serving(stream.cuda_stream)
+        bat = batched_serving(stream.cuda_stream, peak_tflops, peak_src)
     var = None
     if world == 1 and not args.no_variants:
         from paper_2310_01775_gb300 import variants as V
@@ -380,11 +452,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(args, P),
-                           reverse_sweep="time-parallel" if per_rec["rollout_adj"] == 3 else "sequential"),
+                           reverse_sweep={S.STAMP_ADJ_TIME_PARALLEL: "time-parallel",
+                                          S.STAMP_ADJ_SEQUENTIAL: "sequential"}.get(adj_mode, str(adj_mode))),
             "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e,
             "gpu_launches": gpu_launches,
             "kernels_ms_one_step": {k: round(v[0], 3) for k, v in kt_all.items() if v[1]},
+            "secondary": sec,
             "surrogate_vs_plain": sur, "batched_serving": bat, "solver_variants": var}
     print(json.dumps(line), flush=True)
     prob.close()

@@ -197,6 +197,17 @@ stamp_status stamp_set_profiling_mask(stamp_problem* prob, unsigned mask);
 /* ms_out, launches_out: host arrays of STAMP_NKERNELS (either may be NULL). */
 stamp_status stamp_get_kernel_times(stamp_problem* prob, double* ms_out, long long* launches_out);
 
+/* Measured FP32 FMA throughput of the current device, the roof against
+ * which the rollout and reverse-sweep kernels (FP32-ALU bound: contact
+ * forces, friction and integration per substep) are reported.  The paper
+ * has no counterpart; it states no hardware.  Every thread of a grid that
+ * fills each SM runs 8 independent fmaf chains; `launches` timed launches
+ * (CUDA events, after two warm-up launches) on a stream of its own, median
+ * taken; FLOP = 2 per FMA.  Allocates and frees a small buffer, waits for
+ * its launches.
+ *   tflops_out: host, receives TFLOP/s; ms_per_launch_out: host or NULL. */
+stamp_status stamp_fp32_fma_peak(int launches, double* tflops_out, double* ms_per_launch_out);
+
 /* The solves compute each SVGD iteration's RBF bandwidth (pairwise
  * distances and median, which depend on the particles only) on a second
  * stream of the problem's own, concurrently with the iteration's rollouts,
@@ -234,22 +245,27 @@ stamp_status stamp_set_lanes(stamp_problem* prob, int fwd_lanes, int adj_lanes);
  * belongs to someone else's allocator or pool (which must not be bypassed),
  * code that runs where allocating is forbidden, or a device whose memory is
  * already fully reserved -- and so cannot create a stamp_problem.
- * It computes exactly what stamp_svgd_step computes (same kernels, same
- * arguments and layouts) for N <= STAMP_NOALLOC_MAX_N particles of dimension
- * D <= STAMP_NOALLOC_MAX_D; larger sizes are rejected with STAMP_EINVAL.  Its
- * scratch memory (pairwise distances, Stein direction, histograms, counters,
- * bandwidth; about 5.4 MB) is one fixed device array that every GPU loading
- * the library holds until the process exits.
+ * It runs stamp_svgd_step's kernels with the plain RBF kernel (kind 0 of
+ * stamp_set_svgd_kernel) and unit weights, for N <= STAMP_NOALLOC_MAX_N
+ * particles of dimension D <= STAMP_NOALLOC_MAX_D (larger sizes are rejected
+ * with STAMP_EINVAL).  It sums the Stein direction over j in one share where
+ * stamp_svgd_step may split that sum over several CTAs, so the two agree to
+ * within the rounding of that grouping.  Its scratch memory (pairwise
+ * distances, Stein direction, histograms, counters, bandwidth; about 5.4 MB)
+ * is one fixed device array that every GPU loading the library holds until
+ * the process exits.
  *   theta, grad_logp: device N x D, 16-byte aligned; adam_m, adam_v: device
  *   N x D; step >= 1; lr; sgd_phase; h_out, phi_out: device or NULL (as in
  *   stamp_svgd_step); cuda_stream: the cudaStream_t to run on (NULL = legacy
  *   default stream).
  * The first call on a device sets up that device's scratch address (a symbol
- * lookup and one 4-byte copy), so make it before any stream capture.  The
- * call waits for its stream and returns STAMP_ENONFINITE if a non-finite
- * value appeared.  Every call shares the one array and it keeps the last
- * call's contents (the call clears what must start at zero): calls that
- * overlap on the GPU (other streams, other host threads) race. */
+ * lookup, kept for the life of the process: a device reset is not
+ * supported), so make that first call before any stream capture.  Each call
+ * reads back the device error flag and waits for its stream; it returns
+ * STAMP_ENONFINITE if a non-finite value appeared.  Every call shares the one
+ * array and it keeps the last call's contents (the call clears what must
+ * start at zero): calls that overlap on the GPU (other streams, other host
+ * threads) race. */
 #define STAMP_NOALLOC_MAX_N 1024
 #define STAMP_NOALLOC_MAX_D 288
 stamp_status stamp_svgd_step_noalloc(float* theta, const float* grad_logp, int N, int D,

@@ -961,8 +961,9 @@ template <int NB, int L>
 cudaError_t launch(const SimConst& sc, const RolloutArgs& a, bool adjoint, cudaStream_t st) {
     const long long threads_total = (long long)a.N * L;
     // spread over the SMs: small CTAs when there are few particles
+    const int sms = sm_count();
     int cta = 32;
-    while (cta < 128 && threads_total / (cta * 2) >= 152) cta *= 2;
+    while (cta < 128 && threads_total / (cta * 2) >= sms) cta *= 2;
     const int grid = (int)((threads_total + cta - 1) / cta);
     if (!adjoint) {
         rollout_fwd_kernel<NB, L><<<grid, cta, 0, st>>>(sc, a);

@@ -408,6 +408,25 @@ namespace stamp {
 
 void set_last_error(const char* msg) { g_err = msg; }
 
+int sm_count() {
+    constexpr int kDevices = 64;
+    static int cached[kDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
 SimConst problem_const(const stamp_problem* p) { return p->sc; }
 
 stamp_status rollout_from(stamp_problem* p, const float* theta, const float* init_states, int N,

@@ -87,6 +87,10 @@ __host__ __device__ __forceinline__ float u23(uint64_t x) {
 }
 constexpr uint64_t kStreamGumbel = 0, kStreamInit = 1;
 
+// Streaming multiprocessors of the current device (queried once per device),
+// for grid sizing.
+int sm_count();
+
 // Launchers (return the launch error).  `lanes` = threads cooperating on one
 // particle in the rollout kernels.
 cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st);

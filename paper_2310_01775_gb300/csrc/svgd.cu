@@ -12,6 +12,7 @@
 #include <cfloat>
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "stamp_internal.cuh"
 
 namespace stamp {
@@ -236,42 +237,14 @@ __global__ void __launch_bounds__(256) median_digit_batch_kernel(const SvgdInst*
     median_digit_body(g.N, dg, g.d2, g.hist, g.sel, g.counter + dg, g.h, nullptr, it.y, g.med_ctas);
 }
 
-// ---- TMA bulk copies and mbarriers (inline PTX) -----------------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// 1-D bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0),
-// completion counted on `bar` in bytes.
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes,
-                                           uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_async_shared() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-constexpr unsigned kWaitLimit = 1u << 20;   // bounded mbarrier waits (then error flag)
+// TMA bulk copies and mbarriers: the shared helpers of async_copy.cuh, whose
+// kWaitLimit bounds every wait (then the error flag).
+using async::fence_async_shared;
+using async::kWaitLimit;
+using async::mbar_expect_tx;
+using async::mbar_init;
+using async::mbar_try_wait;
+using async::tma_load_1d;
 
 // phi_i = (1/N) sum_j [k_ij g_j + (2/h) k_ij (theta_i - theta_j)], k_ij = exp(-d2_ij/h).
 // A warp owns kR rows; lane l owns columns l, l+32, ...  (DP slots).  The j
@@ -623,7 +596,8 @@ cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch&
 
 cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h_out,
                                 cudaStream_t st) {
-    int grid = N - 1 < 152 * 2 ? N - 1 : 152 * 2;
+    const int cap = 2 * sm_count();
+    int grid = N - 1 < cap ? N - 1 : cap;
     if (grid < 1) grid = 1;
     median_digit_kernel<<<grid, 256, 0, st>>>(N, digit, s.d2, s.hist, s.sel, s.counter + digit,
                                               s.h, h_out);
@@ -638,7 +612,7 @@ cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, cons
     // split the sum over j so that about four CTAs per SM are in flight; the
     // shares start on kTJ-row boundaries (16-byte aligned TMA sources)
     const int row_blocks = (N + kW * kR - 1) / (kW * kR);
-    int want = (4 * 152 + row_blocks - 1) / row_blocks;
+    int want = (4 * sm_count() + row_blocks - 1) / row_blocks;
     want = want < 1 ? 1 : (want > max_shares ? max_shares : want);
     const int j_chunk = ((N + want - 1) / want + kTJ - 1) / kTJ * kTJ;
     *shares = (N + j_chunk - 1) / j_chunk;
@@ -685,7 +659,7 @@ cudaError_t launch_median_digit_batch(const SvgdInst* inst, const int2* items, i
 
 void phi_batch_plan(int N, int* shares, int* j_chunk) {
     const int row_blocks = (N + kW * kR - 1) / (kW * kR);
-    int want = (4 * 152 + row_blocks - 1) / row_blocks;
+    int want = (4 * sm_count() + row_blocks - 1) / row_blocks;
     want = want < 1 ? 1 : (want > kMaxShares ? kMaxShares : want);
     *j_chunk = ((N + want - 1) / want + kTJ - 1) / kTJ * kTJ;
     *shares = (N + *j_chunk - 1) / *j_chunk;

@@ -31,18 +31,23 @@ constexpr size_t kOffHist = kOffPhi + align256((size_t)kMaxN * kMaxD * sizeof(fl
 constexpr size_t kOffSel = kOffHist + align256((2048 + 2048 + 1024) * sizeof(unsigned));
 constexpr size_t kOffCounter = kOffSel + 256;
 constexpr size_t kOffH = kOffCounter + 256;
-constexpr size_t kOffOne = kOffH + 256;
-constexpr size_t kOffFlag = kOffOne + 256;
+constexpr size_t kOffFlag = kOffH + 256;
 constexpr size_t kScratchBytes = kOffFlag + 256;
 
 // The scratch: one array per device that loads this library (about 5.4 MB).
 // In host code `g_noalloc_scratch` is a host-side stand-in, not a device
 // address: kernels get the address that cudaGetSymbolAddress returns.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+// h of the SGD phase; initialised with the module, never written.
+static __device__ __align__(16) float g_noalloc_one = 1.f;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_base[kMaxDevices] = {};
+struct Bases {
+    unsigned char* scratch;
+    const float* one;
+};
+Bases g_base[kMaxDevices] = {};
 
 // Report through stamp_last_error(), like every other call of the library.
 stamp_status noalloc_fail(stamp_status s, const char* msg, cudaError_t e = cudaSuccess) {
@@ -67,24 +72,22 @@ bool on_device(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Device address of the scratch on the current device; set up on the first
-// call per device (symbol lookup and the constant 1.0f used as h in the SGD
-// phase).
-stamp_status scratch_base(unsigned char** out) {
+// Device addresses of the scratch and of the constant 1 on the current
+// device: looked up (cudaGetSymbolAddress, with that device current) on the
+// first call per device and kept for the life of the process.
+stamp_status scratch_base(Bases* out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "cudaGetDevice failed", e);
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(STAMP_EINVAL, "device index too large");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_base[dev]) {
+    if (!g_base[dev].scratch) {
         void* p = nullptr;
+        void* one = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&one, g_noalloc_one);
         if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "cudaGetSymbolAddress failed", e);
-        const float one = 1.f;
-        e = cudaMemcpy(static_cast<unsigned char*>(p) + kOffOne, &one, sizeof one,
-                       cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "scratch set-up failed", e);
-        g_base[dev] = static_cast<unsigned char*>(p);
+        g_base[dev] = Bases{static_cast<unsigned char*>(p), static_cast<const float*>(one)};
     }
     *out = g_base[dev];
     return STAMP_OK;
@@ -108,9 +111,10 @@ extern "C" stamp_status stamp_svgd_step_noalloc(float* theta, const float* grad_
         return noalloc_fail(STAMP_EINVAL, "a pointer is not device memory");
     if ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(grad_logp)) & 15u)
         return noalloc_fail(STAMP_EINVAL, "theta and grad_logp must be 16-byte aligned");
-    unsigned char* base = nullptr;
-    stamp_status st = scratch_base(&base);
+    Bases bases{};
+    stamp_status st = scratch_base(&bases);
     if (st != STAMP_OK) return st;
+    unsigned char* base = bases.scratch;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     stamp::SvgdScratch sc{reinterpret_cast<float*>(base + kOffD2),
                           reinterpret_cast<unsigned*>(base + kOffHist),
@@ -125,7 +129,7 @@ extern "C" stamp_status stamp_svgd_step_noalloc(float* theta, const float* grad_
     if (e != cudaSuccess) return noalloc_fail(STAMP_ECUDA, "clearing the scratch failed", e);
     const float* part = grad_logp;   // SGD phase: phi = grad log rho
     int shares = 1;
-    const float* h_src = reinterpret_cast<const float*>(base + kOffOne);
+    const float* h_src = bases.one;
     if (!sgd_phase) {
         float* phi = reinterpret_cast<float*>(base + kOffPhi);   // room for one share
         e = stamp::launch_pairwise(theta, N, D, sc, s);

@@ -161,7 +161,7 @@ cudaError_t launch_struct_phi(const float* theta, const float* grad, const float
     if (H > kMaxHs) return cudaErrorInvalidValue;
     const int D = H * (M + 2), rows = (N + kRows - 1) / kRows;
     // split the sum over j so that about four CTAs per SM are in flight
-    int want = (4 * 152 + rows - 1) / rows;
+    int want = (4 * sm_count() + rows - 1) / rows;
     want = want < 1 ? 1 : (want > max_shares ? max_shares : want);
     const int j_chunk = ((N + want - 1) / want + kTJ - 1) / kTJ * kTJ;
     *shares = (N + j_chunk - 1) / j_chunk;

@@ -101,6 +101,7 @@ _sigs = {
     "stamp_batch_results": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "stamp_batch_read_theta": [_vp, _i, _vp],
     "stamp_solve_info": [_vp, _vp, _vp],
+    "stamp_fp32_fma_peak": [_i, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -229,6 +230,14 @@ def stamp_svgd_step_noalloc(theta, grad_logp, N, D, adam_m, adam_v, step, lr, sg
                                         _f32(phi_out, "phi_out"), cuda_stream))
 
 
+def stamp_fp32_fma_peak(launches: int = 20) -> tuple[float, float]:
+    """(TFLOP/s, ms per launch): measured FP32 FMA throughput of the current
+    device (independent fmaf chains filling every SM)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.stamp_fp32_fma_peak(int(launches), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -316,6 +325,11 @@ class Problem:
         m = ctypes.c_int()
         _check(_lib.stamp_get_adjoint_mode(self.handle, int(N), ctypes.byref(m)))
         return m.value
+
+    def adjoint_launches(self, N):
+        """Kernel launches of one reverse sweep with N particles (the
+        time-parallel sweep: relaxed parameters, Jacobians, recurrence)."""
+        return {STAMP_ADJ_TIME_PARALLEL: 3}.get(self.adjoint_mode(N), 1)
 
     def set_lanes(self, fwd_lanes, adj_lanes):
         stamp_set_lanes(self.handle, fwd_lanes, adj_lanes)

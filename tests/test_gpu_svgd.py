@@ -36,8 +36,11 @@ def term_scale(theta, g, h):
 @pytest.mark.parametrize("N,name,over", [(1, "pusher1_h2", {}), (2, "pusher1_h2", {}),
                                          (32, "pusher1_h2", {}), (37, "pusher1_h4", {}),
                                          (1024, "pusher1_h4", {}), (2048, "pusher3_h6", {}),
-                                         # the largest particle dimension: 4 blocks, H = 8 (D = 144)
-                                         (300, "pusher3_h6", {"n_blocks": 4, "H": 8})])
+                                         # 4 blocks, H = 8 (D = 144)
+                                         (300, "pusher3_h6", {"n_blocks": 4, "H": 8}),
+                                         # the largest particle dimension the ABI admits:
+                                         # 4 blocks, H = 16 (D = 288, nine columns per lane)
+                                         (320, "pusher3_h6", {"n_blocks": 4, "H": 16})])
 def test_svgd_step_parity(N, name, over):
     prob, P = make_problem(N, name, **over)
     D = prob.D

@@ -30,16 +30,19 @@ def _inputs(N, D, seed):
     return [torch.tensor(x, device="cuda") for x in (theta, g, m, v)]
 
 
-@pytest.mark.parametrize("N,name,sgd", [(37, "pusher1_h4", 0), (1024, "pusher1_h4", 0),
-                                        (300, "pusher3_h6", 0), (64, "pusher1_h2", 1),
-                                        (1, "pusher1_h2", 0)])
-def test_noalloc_step_matches_problem_step_twice(N, name, sgd):
+@pytest.mark.parametrize("N,name,sgd,over", [(37, "pusher1_h4", 0, {}), (1024, "pusher1_h4", 0, {}),
+                                             (300, "pusher3_h6", 0, {}), (64, "pusher1_h2", 1, {}),
+                                             (1, "pusher1_h2", 0, {}),
+                                             # the documented limits: N = 1024, D = 288 (4 blocks, H = 16)
+                                             (1024, "pusher3_h6", 0, {"n_blocks": 4, "H": 16})])
+def test_noalloc_step_matches_problem_step_twice(N, name, sgd, over):
     from paper_2310_01775_gb300 import stamp as S
-    P = W.params(name)
+    P = W.params(name, **over)
     init, goal = W.scene(P, 0)
     stream = torch.cuda.current_stream().cuda_stream
     prob = S.Problem(P, init, goal, N, stream)
     D = prob.D
+    assert N <= 1024 and D <= 288
     a = _inputs(N, D, 40 + N)                      # problem-based path
     b = [x.clone() for x in a]                     # allocation-free path
     for step in (3, 4):                            # two calls in a row, state carried over
