@@ -41,7 +41,7 @@ FP32_LANES = 128                    # FP32 lanes per SM; 1 FMA = 2 FLOP
 # capture of the workload, valid while the kernel sources are unchanged
 # (sha256 prefix over the rollout sources at capture time).
 TRAFFIC = {}
-ROLLOUT_SOURCES = ("rollout.cuh", "adjoint_time.cu", "adjoint_replay.cu")
+ROLLOUT_SOURCES = ("rollout.cuh", "adjoint_time.cu")
 
 
 def peaks():
@@ -291,7 +291,8 @@ def secondary_workload(name, seed, flush, stream, steps=5, warmup=3):
     prob = S.Problem(P, init, goal, P["N"], stream.cuda_stream)
     ms = time_solves(prob, P, P["N"], seed, steps, warmup, flush, stream)
     units = P["N"] * P["H"] * P["T"] * P["svgd_iters"]
-    mode = "time-parallel" if prob.adjoint_mode(P["N"]) == S.STAMP_ADJ_TIME_PARALLEL else "sequential"
+    mode = {S.STAMP_ADJ_TIME_PARALLEL: "time-parallel", S.STAMP_ADJ_REPLAY: "segment replay + sequential",
+            S.STAMP_ADJ_SEQUENTIAL: "sequential"}[prob.adjoint_mode(P["N"])]
     prob.close()
     return {"workload": f"{name}: {P['n_blocks']} block(s), H={P['H']}, T={P['T']}, N={P['N']}, "
                         f"C={P['ckpt_every']}, {P['svgd_iters']} SVGD iterations per step",
@@ -453,6 +454,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(args, P),
                            reverse_sweep={S.STAMP_ADJ_TIME_PARALLEL: "time-parallel",
+                                          S.STAMP_ADJ_REPLAY: "segment replay + sequential",
                                           S.STAMP_ADJ_SEQUENTIAL: "sequential"}.get(adj_mode, str(adj_mode))),
             "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e,

@@ -150,6 +150,34 @@ stamp_status stamp_svgd_step(stamp_problem* prob, float* theta, const float* gra
                              float* adam_m, float* adam_v, int step, float lr, int sgd_phase,
                              float* h_out, float* phi_out);
 
+/* ---- Particle shards (one Stein iteration over several GPUs) -------------
+ * Eq. svgd sums over all particles j, but the rollout, its reverse sweep and
+ * the update of particle i need only particle i: a set of N particles can be
+ * split into contiguous shards, one per GPU.  Each shard rolls out its own
+ * rows, the shards exchange theta and grad log rho (an all-gather of N x D
+ * floats each, done by the caller, e.g. with NCCL), and each computes the
+ * bandwidth from all N (the same value everywhere) and the Stein direction
+ * and Adam step of its own rows.  With the offsets below, the shards
+ * together compute bit for bit what one problem computes for all N.
+ *
+ * stamp_set_particle_offset: later rollouts of this problem treat their row
+ * r as particle particle0 + r of the full set (its Gumbel draws, Eq.
+ * gamma_map); 0 (the default) for an unsharded problem. */
+stamp_status stamp_set_particle_offset(stamp_problem* prob, int particle0);
+/* The update of rows [row0, row0 + rows) of an N-particle set:
+ *   theta_all, grad_all: device N x D, the gathered particles and
+ *     grad log rho (16-byte aligned);
+ *   theta_rows: device rows x D, this shard's particles, updated in place;
+ *   adam_m, adam_v: device rows x D, this shard's moments;
+ *   step, lr, sgd_phase, h_out: as in stamp_svgd_step;
+ *   phi_out: device rows x D or NULL.
+ * N <= max_particles (the N x N distances live in the problem).  The RBF
+ * kernel only (kind 0), unit weights. */
+stamp_status stamp_svgd_step_rows(stamp_problem* prob, const float* theta_all, const float* grad_all,
+                                  int N, int row0, int rows, float* theta_rows, float* adam_m,
+                                  float* adam_v, int step, float lr, int sgd_phase, float* h_out,
+                                  float* phi_out);
+
 /* Algorithm 1 end to end: svgd_iters SVGD updates then sgd_iters SGD
  * updates (iteration it uses Gumbel noise (seed, it) and Adam step it+1),
  * then the hard evaluation of every particle (Gamma, no noise) and the
@@ -178,7 +206,7 @@ stamp_status stamp_sync(stamp_problem* prob);
  * totals are gathered at stamp_sync / stamp_solve.  Kernel ids: */
 enum {
     STAMP_K_ROLLOUT_FWD = 0,  /* forward rollout (relaxed or hard) */
-    STAMP_K_ROLLOUT_ADJ = 1,  /* reverse sweep (time-parallel: its three launches together) */
+    STAMP_K_ROLLOUT_ADJ = 1,  /* reverse sweep (time-parallel or replay: all its launches together) */
     STAMP_K_PAIRWISE = 2,     /* pairwise distances + first median digit */
     STAMP_K_MEDIAN = 3,       /* remaining median digits */
     STAMP_K_PHI = 4,          /* Stein direction */
@@ -225,17 +253,38 @@ stamp_status stamp_set_overlap(stamp_problem* prob, int enable);
  * particle runs backwards.  Scratch: 44 floats per particle and substep,
  * allocated at create (not when it would exceed 4 GiB).
  * STAMP_ADJ_SEQUENTIAL: each particle's team differentiates substep after
- * substep (segment replay for ckpt_every > 1); every other scene uses it.
+ * substep, recomputing each segment of ckpt_every substeps from its
+ * checkpoint on the same serial path.
+ * STAMP_ADJ_REPLAY applies to ckpt_every > 1: one launch rebuilds the states
+ * before every substep from the checkpoints for all (particle, segment)
+ * pairs at once (the segments are independent given their checkpoints),
+ * into a scratch tape of interval 1 ((H*T + 1) x N x S floats, allocated at
+ * create when at most 4 GiB); then the sequential sweep runs on that tape
+ * with nothing to recompute.  The forward still stores only every
+ * ckpt_every-th state.
  * STAMP_ADJ_AUTO (the default): time-parallel where it applies, for up to
  * 3072 particles (beyond that the sequential teams fill the GPU and the
- * Jacobians' extra arithmetic costs more than it saves), else sequential.
- * Both sweeps give the gradient of the same float32 simulation, with sums
+ * Jacobians' extra arithmetic costs more than it saves), else the replay
+ * where it applies, else sequential.
+ * All sweeps give the gradient of the same float32 simulation, with sums
  * taken in a different order. */
-enum { STAMP_ADJ_SEQUENTIAL = 0, STAMP_ADJ_TIME_PARALLEL = 1, STAMP_ADJ_AUTO = 2 };
+enum { STAMP_ADJ_SEQUENTIAL = 0, STAMP_ADJ_TIME_PARALLEL = 1, STAMP_ADJ_AUTO = 2,
+       STAMP_ADJ_REPLAY = 3 };
 stamp_status stamp_set_adjoint_mode(stamp_problem* prob, int mode);
-/* The sweep (STAMP_ADJ_SEQUENTIAL or STAMP_ADJ_TIME_PARALLEL) that a call
- * with N particles uses. */
+/* The sweep (STAMP_ADJ_SEQUENTIAL, STAMP_ADJ_TIME_PARALLEL or
+ * STAMP_ADJ_REPLAY) that a call with N particles uses. */
 stamp_status stamp_get_adjoint_mode(stamp_problem* prob, int N, int* mode);
+
+/* Failure-detection test hook (no paper counterpart).  The next launch of
+ * the RBF Stein-direction kernel on this problem (stamp_svgd_step or a
+ * solve's SVGD iteration) runs with each CTA's first shared-memory stage
+ * armed on its mbarrier but its bulk copy never issued, and with its waits
+ * bounded at 4096 polls: the wait runs out, the CTA waits (bounded) for its
+ * other copy in flight, raises the device error flag and returns, and the
+ * next stamp_sync / stamp_solve reports STAMP_ETIMEOUT.  No GPU fault, trap
+ * or hang is involved; that step's results are not valid.  One-shot: later
+ * calls run normally. */
+stamp_status stamp_inject_wait_timeout(stamp_problem* prob);
 
 /* Lanes per particle used by the rollout kernels (1,2,4,8,16,32; 0 = automatic). */
 stamp_status stamp_set_lanes(stamp_problem* prob, int fwd_lanes, int adj_lanes);

@@ -306,7 +306,8 @@ __global__ void relax_kernel(const SimConst sc, const RolloutArgs a, float* __re
     const bool noise = a.iter >= 0;
     const uint64_t gkey = noise ? sm64(sm64(a.seed, kStreamGumbel), (uint64_t)a.iter) : 0ull;
     float z[4], uu, vv;
-    relax_action<1>(sc, a.theta + (size_t)i * sc.D, k, i, gkey, noise, a.hard != 0, z, uu, vv);
+    relax_action<1>(sc, a.theta + (size_t)i * sc.D, k, i + a.particle0, gkey, noise, a.hard != 0,
+                    z, uu, vv);
     float* r = rel + (size_t)k * kRel * a.N + i;
     r[0] = z[0];
     r[a.N] = z[1];

@@ -469,65 +469,164 @@ mlp_bwd_kernel(const float* __restrict__ dy, int rows, int out_dim, int n_tiles,
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// Element (row r, column c) of consecutive K-column BF16 tiles of 128 rows,
-// `stride` bytes apart.
-__device__ __forceinline__ float tiled_at(const unsigned char* base, size_t stride, int r, int c,
-                                          int K) {
-    const unsigned short h = *reinterpret_cast<const unsigned short*>(
-        base + (size_t)(r >> 7) * stride + tile_off(r & 127, c, K));
-    return __uint_as_float((unsigned)h << 16);
+// 8x8 transpose of 16-bit elements across a warp: thread t holds row t/4,
+// columns 2(t%4) and 2(t%4)+1 before and after.
+__device__ __forceinline__ unsigned transpose8x8(unsigned x) {
+    unsigned y;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(y) : "r"(x));
+    return y;
 }
 
-// dW_l (out_r x in_r, FP32, added to) += sum over rows of dz_l[r][o] a_l[r][i]:
-// 64 x 64 output tiles, rows split over blockIdx.z, FP32 accumulation on
-// CUDA cores, one atomic add per output and block.
-__global__ void __launch_bounds__(256) mlp_dw_kernel(const unsigned char* __restrict__ a, int Ka,
-                                                     size_t a_stride,
-                                                     const unsigned char* __restrict__ dz, int Kd,
-                                                     int rows, int out_r, int in_r, int row_chunk,
-                                                     float* __restrict__ dW) {
-    __shared__ float ds[32][65], as[32][65];
-    const int o0 = blockIdx.y * 64, i0 = blockIdx.x * 64;
-    const int rb = blockIdx.z * row_chunk, re = min(rows, rb + row_chunk);
-    const int to = threadIdx.x / 16, ti = threadIdx.x % 16;
-    float acc[4][4] = {};
-    for (int r0 = rb; r0 < re; r0 += 32) {
-        for (int t = threadIdx.x; t < 32 * 64; t += 256) {
-            const int rr = t / 64, cc = t % 64, r = r0 + rr;
-            ds[rr][cc] = (r < re && o0 + cc < out_r) ? tiled_at(dz, kActBytes, r, o0 + cc, Kd) : 0.f;
-            as[rr][cc] = (r < re && i0 + cc < in_r) ? tiled_at(a, a_stride, r, i0 + cc, Ka) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            float dv[4], av[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) { dv[p] = ds[k][to * 4 + p]; av[p] = as[k][ti * 4 + p]; }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(dv[p], av[q], acc[p][q]);
-        }
-        __syncthreads();
+// Weight gradient of one layer on the tensor cores: the sum over rows of
+// outer products is an MMA whose reduction dimension K is the rows.  The
+// saved activations and dz tiles are K-major with K = units (a 128-byte core
+// matrix = 8 rows x 8 units); for this MMA the units become M and N and the
+// rows become K, so each core matrix is transposed (movmatrix) into the
+// K-major operand layout in shared memory:
+//   D (M = 128 units of P per blockIdx.x) x (N = NQ units of Q)
+//     += P^T (M x 128 rows) . Q (128 rows x N)      per 128-row tile,
+// accumulated in TMEM over the tiles of this CTA's row split (blockIdx.y),
+// then stored as the split's partial; a second kernel sums the splits in
+// order (deterministic: no atomics).  The bias gradient of the dz operand's
+// units is summed from the transposed operand, rows in order, per split.
+constexpr int kDwMaxSplits = 128;
+struct DwSmem {
+    alignas(128) unsigned char A[kRows * kRows * 2];     // 32 KB: 128 units x 128 rows
+    alignas(128) unsigned char B[kHidden * kRows * 2];   // 64 KB: up to 256 units x 128 rows
+    uint64_t mma_bar;
+    unsigned tmem_slot;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+mlp_dw_tc_kernel(const unsigned char* __restrict__ P, int KP, size_t p_stride,
+                 const unsigned char* __restrict__ Q, int NQ, size_t q_stride, int n_tiles,
+                 int tiles_per_split, float* __restrict__ part, float* __restrict__ dbp,
+                 int dz_is_P, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    DwSmem& sm = *reinterpret_cast<DwSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned cols = NQ <= 32 ? 32u : NQ <= 64 ? 64u : NQ <= 128 ? 128u : 256u;
+    if (tid == 0) {
+        mbar_init(&sm.mma_bar, 1);
+        fence_async_shared();
     }
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int o = o0 + to * 4 + p, i = i0 + ti * 4 + q;
-            if (o < out_r && i < in_r) atomicAdd(&dW[(size_t)o * in_r + i], acc[p][q]);
+    if (warp == 0) tmem_alloc(&sm.tmem_slot, cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = sm.tmem_slot;
+    const int mb = blockIdx.x, split = blockIdx.y;
+    const int t0 = split * tiles_per_split, t1 = min(n_tiles, t0 + tiles_per_split);
+    // the dz operand's units whose bias gradient this CTA sums (thread u: unit u)
+    const int n_bias = dz_is_P ? kRows : (mb == 0 ? NQ : 0);
+    const unsigned char* bias_src = dz_is_P ? sm.A : sm.B;
+    float bsum = 0.f;
+    unsigned mma_phase = 0;
+    bool failed = false, mma_pending = false;
+    const int nA = 16 * 16, nB = 16 * (NQ / 8);
+    for (int t = t0; t < t1 && !failed; ++t) {
+        const unsigned char* Pt = P + (size_t)t * p_stride;
+        const unsigned char* Qt = Q + (size_t)t * q_stride;
+        // core matrix c: row group gs (8 rows) of unit group gu, transposed
+        for (int c = warp; c < nA + nB; c += kThreads / 32) {
+            const bool isA = c < nA;
+            const int cc = isA ? c : c - nA, gs = cc & 15, gu = cc >> 4;
+            const unsigned char* src = isA ? Pt + gs * (KP / 8) * 128 + (mb * 16 + gu) * 128
+                                           : Qt + gs * (NQ / 8) * 128 + gu * 128;
+            unsigned char* dst = (isA ? sm.A : sm.B) + gu * 2048 + gs * 128;
+            const int off = (lane >> 2) * 16 + (lane & 3) * 4;
+            *reinterpret_cast<unsigned*>(dst + off) =
+                transpose8x8(__ldg(reinterpret_cast<const unsigned*>(src + off)));
         }
+        fence_async_shared();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_bf16(kRows, NQ);
+            for (int kk = 0; kk < kRows / 16; ++kk)
+                mma_bf16(tmem, smem_desc(sm.A + kk * 256, 128, 2048),
+                         smem_desc(sm.B + kk * 256, 128, 2048), idesc, (t > t0 || kk > 0) ? 1u : 0u);
+            mma_commit(&sm.mma_bar);
+        }
+        mma_pending = true;
+        if (tid < n_bias) {   // bias gradient: this unit's row of the operand, rows in order
+            const unsigned char* rowp = bias_src + (tid >> 3) * 2048 + (tid & 7) * 16;
+            for (int g = 0; g < kRows / 8; ++g) {
+                const uint4 q = *reinterpret_cast<const uint4*>(rowp + g * 128);
+                const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) bsum += bf_lo(w[e]) + bf_hi(w[e]);
+            }
+        }
+        unsigned spins = 0;
+        bool ok = true;
+        while (!(ok = mbar_try_wait(&sm.mma_bar, mma_phase)) && ++spins < kWaitLimit) {
+        }
+        if (__syncthreads_or(!ok)) { failed = true; break; }   // the MMA stays pending
+        mma_phase ^= 1u;
+        mma_pending = false;
+        tc_fence_after();
+    }
+    if (!failed) {
+        // epilogue: TMEM lane = unit of P (row of D), column = unit of Q
+        const int quarter = warp & 3, cpart = warp >> 2, row = quarter * 32 + lane;
+        const unsigned lane_base = tmem + ((unsigned)(quarter * 32) << 16);
+        float* out = part + ((size_t)split * gridDim.x * kRows + mb * kRows + row) * NQ;
+        if (NQ >= 128) {
+            for (int c0 = cpart * (NQ / 4); c0 < (cpart + 1) * (NQ / 4); c0 += 32) {
+                float v[32];
+                tmem_ld32(lane_base + c0, v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    reinterpret_cast<float4*>(out + c0)[q] =
+                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        } else if (cpart == 0 && NQ == 32) {
+            float v[32];
+            tmem_ld32(lane_base, v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                reinterpret_cast<float4*>(out)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else if (cpart == 0) {   // NQ == 16
+            float v[16];
+            tmem_ld16(lane_base, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                reinterpret_cast<float4*>(out)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        if (tid < n_bias) dbp[(size_t)split * kHidden + (dz_is_P ? mb * kRows : 0) + tid] = bsum;
+    }
+    if (failed && tid == 0) {
+        atomicOr(err, 2);
+        if (mma_pending)
+            for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&sm.mma_bar, mma_phase); ++w) {
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, cols);
 }
 
-// db_l[o] += sum over rows of dz_l[r][o].
-__global__ void mlp_db_kernel(const unsigned char* __restrict__ dz, int Kd, int rows, int out_r,
-                              int row_chunk, float* __restrict__ db) {
-    const int o = threadIdx.x;
-    if (o >= out_r) return;
-    const int rb = blockIdx.x * row_chunk, re = min(rows, rb + row_chunk);
-    float s = 0.f;
-    for (int r = rb; r < re; ++r) s += tiled_at(dz, kActBytes, r, o, Kd);
-    atomicAdd(&db[o], s);
+// dW (real sizes out_r x in_r, added to) and db (out_r, added to) from the
+// splits' partials, summed in split order.  part: [split][M][NQ] with
+// M = units of P; transpose: P holds the layer's inputs (D = dW^T).
+__global__ void mlp_dw_reduce_kernel(const float* __restrict__ part, const float* __restrict__ dbp,
+                                     int splits, int M, int NQ, int transpose, int out_r, int in_r,
+                                     float* __restrict__ dW, float* __restrict__ db) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < M * NQ) {
+        float s = 0.f;
+        for (int q = 0; q < splits; ++q) s += part[(size_t)q * M * NQ + e];
+        const int m = e / NQ, n = e % NQ;
+        const int o = transpose ? n : m, i = transpose ? m : n;
+        if (o < out_r && i < in_r) dW[(size_t)o * in_r + i] += s;
+    }
+    if (e < out_r) {
+        float s = 0.f;
+        for (int q = 0; q < splits; ++q) s += dbp[(size_t)q * kHidden + e];
+        db[e] += s;
+    }
 }
 
 // Mean squared error over rows x out_dim: dy = 2 (y - t) / n, loss += sum (y-t)^2 / n.
@@ -606,24 +705,47 @@ cudaError_t backward(const float* dy, int rows, int in_dim, int out_dim,
     return cudaGetLastError();
 }
 
+size_t dw_part_floats() { return (size_t)kDwMaxSplits * (kHidden * kHidden + kHidden); }
+
 cudaError_t weight_grads(const unsigned char* x_tiled, const unsigned char* saved,
                          const unsigned char* dzsave, int tile_base, int tile_cap, int rows,
-                         int in_dim, int out_dim, float* grad, cudaStream_t st) {
-    const int chunk = 512;
+                         int in_dim, int out_dim, float* grad, float* part, int* err, int sm_count,
+                         cudaStream_t st) {
+    const int n_tiles = (rows + kRows - 1) / kRows;
+    const size_t smem = sizeof(DwSmem) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(mlp_dw_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    float* dbp = part + (size_t)kDwMaxSplits * kHidden * kHidden;
     for (int l = 0; l < kLayers; ++l) {
         const int in_r = l == 0 ? in_dim : kHidden, out_r = l == 3 ? out_dim : kHidden;
         const unsigned char* a = l == 0 ? x_tiled + (size_t)tile_base * kInBytes
                                         : saved + ((size_t)l * tile_cap + tile_base) * kActBytes;
         const size_t a_stride = l == 0 ? kInBytes : kActBytes;
         const unsigned char* dz = dzsave + ((size_t)l * tile_cap + tile_base) * kActBytes;
+        // P: the operand of 256 units (M in 128-unit blocks); Q: the other one
+        const bool dz_is_P = layer_n(l) == kHidden;
+        const unsigned char* P = dz_is_P ? dz : a;
+        const unsigned char* Q = dz_is_P ? a : dz;
+        const int KP = dz_is_P ? layer_n(l) : layer_k(l), NQ = dz_is_P ? layer_k(l) : layer_n(l);
+        const size_t p_stride = dz_is_P ? kActBytes : a_stride, q_stride = dz_is_P ? a_stride : kActBytes;
+        const int mblocks = KP / kRows;
+        int splits = sm_count / mblocks;
+        splits = splits < 1 ? 1 : splits > kDwMaxSplits ? kDwMaxSplits : splits;
+        splits = splits > n_tiles ? n_tiles : splits;
+        const int per = (n_tiles + splits - 1) / splits;
+        splits = (n_tiles + per - 1) / per;
+        mlp_dw_tc_kernel<<<dim3(mblocks, splits), kThreads, smem, st>>>(
+            P, KP, p_stride, Q, NQ, q_stride, n_tiles, per, part, dbp, dz_is_P ? 1 : 0, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         float* dW = grad + param_offset(l, in_dim, out_dim);
-        const dim3 grid((in_r + 63) / 64, (out_r + 63) / 64, (rows + chunk - 1) / chunk);
-        mlp_dw_kernel<<<grid, 256, 0, st>>>(a, layer_k(l), a_stride, dz, layer_n(l), rows, out_r,
-                                            in_r, chunk, dW);
-        mlp_db_kernel<<<(rows + chunk - 1) / chunk, 256, 0, st>>>(dz, layer_n(l), rows, out_r, chunk,
-                                                                 dW + (size_t)out_r * in_r);
+        mlp_dw_reduce_kernel<<<(KP * NQ + 255) / 256, 256, 0, st>>>(
+            part, dbp, splits, KP, NQ, dz_is_P ? 0 : 1, out_r, in_r, dW, dW + (size_t)out_r * in_r);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t mse(const float* y, const float* t, int n, float* dy, float* loss, cudaStream_t st) {
@@ -651,6 +773,7 @@ struct stamp_mlp {
     unsigned char *saved = nullptr, *zsave = nullptr, *dzsave = nullptr;
     float *bias = nullptr, *ypad = nullptr, *ytrain = nullptr, *dy = nullptr;
     float *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr, *loss = nullptr;
+    float* dw_part = nullptr;   // per-split partial weight gradients (deterministic reduction)
     int* err = nullptr;
     int step = 0;
 };
@@ -704,12 +827,13 @@ extern "C" stamp_status stamp_mlp_create(int in_dim, int out_dim, int max_rows, 
     void** dst[] = {(void**)&m->w_tiled, (void**)&m->wt_tiled, (void**)&m->x_tiled, (void**)&m->bias,
                     (void**)&m->ypad,    (void**)&m->saved,    (void**)&m->zsave,   (void**)&m->dzsave,
                     (void**)&m->ytrain,  (void**)&m->dy,       (void**)&m->grad,    (void**)&m->adam_m,
-                    (void**)&m->adam_v,  (void**)&m->loss,     (void**)&m->err};
+                    (void**)&m->adam_v,  (void**)&m->loss,     (void**)&m->err,     (void**)&m->dw_part};
     const size_t bytes[] = {kWeightBytes, kWeightBytes, xt * 128 * kIn * 2, (size_t)kLayers * kHidden * 4,
                             (size_t)max_rows * kOut * 4, 4 * cap * kRows * kHidden * 2,
                             3 * cap * kRows * kHidden * 2, 4 * cap * kRows * kHidden * 2,
                             (size_t)train_rows * out_dim * 4, (size_t)train_rows * out_dim * 4,
-                            np * 4, np * 4, np * 4, 4, 4};
+                            np * 4, np * 4, np * 4, 4, 4,
+                            train_rows > 0 ? dw_part_floats() * 4 : 0};
     size_t total = 0;
     for (size_t b : bytes) total += (b + 255) / 256 * 256;
     cudaError_t e = cudaMalloc(&m->arena, total);
@@ -778,7 +902,8 @@ extern "C" stamp_status stamp_mlp_backward(stamp_mlp* m, const float* dy, int ro
     if (dparams) {
         MLP_TRY(cudaMemsetAsync(dparams, 0, m->n_params * 4, m->stream), "memset failed");
         MLP_TRY(stamp::mlp::weight_grads(m->x_tiled, m->saved, m->dzsave, tile_base, m->tile_cap,
-                                         rows, m->in_dim, m->out_dim, dparams, m->stream),
+                                         rows, m->in_dim, m->out_dim, dparams, m->dw_part, m->err,
+                                         m->sm_count, m->stream),
                 "weight-gradient launch failed");
     }
     return STAMP_OK;
@@ -809,7 +934,8 @@ extern "C" stamp_status stamp_mlp_train(stamp_mlp* m, float* params, const float
                                          m->stream), "MLP backward launch failed");
             MLP_TRY(cudaMemsetAsync(m->grad, 0, m->n_params * 4, m->stream), "memset failed");
             MLP_TRY(stamp::mlp::weight_grads(m->x_tiled, m->saved, m->dzsave, 0, m->tile_cap, batch,
-                                             m->in_dim, m->out_dim, m->grad, m->stream),
+                                             m->in_dim, m->out_dim, m->grad, m->dw_part, m->err,
+                                             m->sm_count, m->stream),
                     "weight-gradient launch failed");
             MLP_TRY(stamp::mlp::adam(params, m->grad, m->adam_m, m->adam_v, (int)m->n_params,
                                      ++m->step, lr, m->stream), "Adam launch failed");

@@ -53,10 +53,15 @@ cudaError_t backward(const float* dy, int rows, int in_dim, int out_dim,
                      const unsigned char* wt_tiled, const unsigned char* zsave,
                      unsigned char* dzsave, int tile_base, int tile_cap, float* dx, int* err,
                      int sm_count, cudaStream_t st);
-// grad (packed like the parameters; must be zero) += dL/dW_l, dL/db_l.
+// grad (packed like the parameters) += dL/dW_l, dL/db_l, on the tensor
+// cores (BF16 operands, FP32 accumulation in TMEM), reduced over row splits
+// in a fixed order; part: dw_part_floats() floats of scratch; err: bit 2 if
+// a bounded wait gave up.
+size_t dw_part_floats();
 cudaError_t weight_grads(const unsigned char* x_tiled, const unsigned char* saved,
                          const unsigned char* dzsave, int tile_base, int tile_cap, int rows,
-                         int in_dim, int out_dim, float* grad, cudaStream_t st);
+                         int in_dim, int out_dim, float* grad, float* part, int* err, int sm_count,
+                         cudaStream_t st);
 cudaError_t mse(const float* y, const float* t, int n, float* dy, float* loss, cudaStream_t st);
 cudaError_t adam(float* p, const float* g, float* m, float* v, int n, int step, float lr,
                  cudaStream_t st);

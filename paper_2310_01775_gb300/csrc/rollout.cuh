@@ -418,7 +418,7 @@ __device__ __forceinline__ void fwd_team(const SimConst& sc, const RolloutArgs& 
 
     for (int k = 0; k < sc.H; ++k) {
         float z[M], uu, vv;
-        relax_action<NB>(sc, th, k, i, gkey, noise, a.hard != 0, z, uu, vv);
+        relax_action<NB>(sc, th, k, i + a.particle0, gkey, noise, a.hard != 0, z, uu, vv);
         const float off = sc.off_max * tanhf(uu);
         const float dist = sc.dist_max * sigmoidf_(vv);
         dsum += dist * dist;
@@ -814,7 +814,7 @@ __device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& 
         Blocks<NB> s0;
         load_state(tape_i + (size_t)(k * segs) * ck2, s0);
         float z[M], uu, vv;
-        relax_action<NB>(sc, th, k, i, gkey, noise, hard, z, uu, vv);
+        relax_action<NB>(sc, th, k, i + a.particle0, gkey, noise, hard, z, uu, vv);
         const float tu = tanhf(uu);
         const float off = sc.off_max * tu;
         const float sg = sigmoidf_(vv);
@@ -954,6 +954,70 @@ __global__ void __launch_bounds__(128) rollout_adj_batch_kernel(const SimConst s
     bool on;
     if (!batch_team<NB>(sc0, b, gtid / L, sc, a, i, on)) return;
     adj_team<NB, L>(sc, a, i, on, gtid & (L - 1));
+}
+
+// ------------------------------ segment replay --------------------------------
+// The checkpointed reverse sweep needs the state before every substep.  The
+// replay rebuilds them for all (particle, segment) pairs at once: team
+// t = g*N + i recomputes segment g (of the H*T/C) of particle i from its
+// checkpoint, with the action's relaxation and pushers placed from the
+// action-start checkpoint exactly as the forward placed them, and writes the
+// C states before its substeps into `full`, laid out [H*T + 1][N][S] like a
+// tape of interval 1 (the last segment's team adds the final state).  What
+// stays serial per particle is the sweep over that tape; the recomputation
+// runs as one throughput-bound launch.
+template <int NB, int L>
+__global__ void __launch_bounds__(128) replay_kernel(const SimConst sc, const RolloutArgs a,
+                                                     float* __restrict__ full) {
+    constexpr int M = Dims<NB>::M, S = Dims<NB>::S;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = (int)(gtid & (L - 1));
+    const long long teams = (long long)a.N * sc.n_ckpt;
+    long long t = gtid / L;
+    const bool on = t < teams;
+    if (!on) t = teams - 1;   // surplus teams shadow the last pair, store nothing
+    const int g = (int)(t / a.N), i = (int)(t % a.N);
+    const int segs = sc.T / sc.C, k = g / segs, sg = g % segs;
+    const size_t ck2 = (size_t)a.N * (S / 2);   // float2 per tape row
+    const float2* tape_i = reinterpret_cast<const float2*>(a.tape + (size_t)i * S);
+    float2* full_i = reinterpret_cast<float2*>(full + (size_t)i * S);
+    const bool noise = a.iter >= 0;
+    const uint64_t gkey = noise ? sm64(sm64(a.seed, kStreamGumbel), (uint64_t)a.iter) : 0ull;
+
+    Blocks<NB> s0, s;
+    load_state(tape_i + (size_t)(k * segs) * ck2, s0);
+    load_state(tape_i + (size_t)g * ck2, s);
+    float z[M], uu, vv;
+    relax_action<NB>(sc, a.theta + (size_t)i * sc.D, k, i + a.particle0, gkey, noise,
+                     a.hard != 0, z, uu, vv);
+    Slots<NB, L> sl;
+    make_slots<NB, L>(sc, s0, lane, z, sc.off_max * tanhf(uu), sc.dist_max * sigmoidf_(vv), sl);
+    Corners<NB, L> cn;
+    make_corners(cn, lane);
+    const int t0 = k * sc.T + sg * sc.C;   // the segment's first substep
+    for (int jj = 0; jj < sc.C; ++jj) {
+        store_state<NB, L>(full_i + (size_t)(t0 + jj) * ck2, s, lane, on);
+        if (jj + 1 == sc.C) break;          // the state after it is the next checkpoint
+        float cs[NB], sn[NB];
+        trig(s, cs, sn);
+        float Fx[NB], Fy[NB], Tq[NB];
+        substep_forces<NB, L>(sc, s, cs, sn, sl, cn, (float)(sg * sc.C + jj + 1), Fx, Fy, Tq);
+        integrate(sc, s, Fx, Fy, Tq);
+    }
+    if (g == sc.n_ckpt - 1) {
+        load_state(tape_i + (size_t)sc.n_ckpt * ck2, s);
+        store_state<NB, L>(full_i + (size_t)(sc.H * sc.T) * ck2, s, lane, on);
+    }
+}
+
+template <int NB, int L>
+cudaError_t launch_replay(const SimConst& sc, const RolloutArgs& a, float* full, cudaStream_t st) {
+    const long long threads_total = (long long)a.N * sc.n_ckpt * L;
+    const int cta = 128;
+    const long long grid = (threads_total + cta - 1) / cta;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    replay_kernel<NB, L><<<(unsigned)grid, cta, 0, st>>>(sc, a, full);
+    return cudaGetLastError();
 }
 
 // ------------------------------ launch --------------------------------------

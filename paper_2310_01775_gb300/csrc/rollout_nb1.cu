@@ -23,4 +23,14 @@ cudaError_t launch_rollout_batch_nb1(const SimConst& sc, const BatchArgs& b, int
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_replay_nb1(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
+                                cudaStream_t st) {
+    switch (lanes) {
+        case 1: return rollout::launch_replay<1, 1>(sc, a, full, st);
+        case 2: return rollout::launch_replay<1, 2>(sc, a, full, st);
+        case 4: return rollout::launch_replay<1, 4>(sc, a, full, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace stamp

@@ -25,4 +25,15 @@ cudaError_t launch_rollout_batch_nb2(const SimConst& sc, const BatchArgs& b, int
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_replay_nb2(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
+                                cudaStream_t st) {
+    switch (lanes) {
+        case 2: return rollout::launch_replay<2, 2>(sc, a, full, st);
+        case 4: return rollout::launch_replay<2, 4>(sc, a, full, st);
+        case 8: return rollout::launch_replay<2, 8>(sc, a, full, st);
+        case 16: return rollout::launch_replay<2, 16>(sc, a, full, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace stamp

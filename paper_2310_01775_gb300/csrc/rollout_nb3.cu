@@ -23,4 +23,14 @@ cudaError_t launch_rollout_batch_nb3(const SimConst& sc, const BatchArgs& b, int
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_replay_nb3(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
+                                cudaStream_t st) {
+    switch (lanes) {
+        case 8: return rollout::launch_replay<3, 8>(sc, a, full, st);
+        case 16: return rollout::launch_replay<3, 16>(sc, a, full, st);
+        case 32: return rollout::launch_replay<3, 32>(sc, a, full, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace stamp

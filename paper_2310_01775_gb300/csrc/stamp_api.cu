@@ -39,6 +39,7 @@ constexpr long long kMaxStatsIters = 1 << 20;
 // substep; above this it is not set up (the sequential sweep runs)
 constexpr size_t kMaxTimeParallelBytes = (size_t)4 << 30;
 constexpr int kTimeParallelMaxN = 3072;   // the automatic mode's crossover (see time_parallel)
+constexpr unsigned kInjectedWaitLimit = 4096;   // polls of a wait made to run out (test hook)
 
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes at;
@@ -62,9 +63,11 @@ struct stamp_problem {
     unsigned *hist = nullptr, *stats = nullptr, *sel = nullptr, *counter = nullptr, *stop = nullptr;
     int *flag = nullptr, *topk = nullptr;
     unsigned long long* dropped = nullptr;
+    // global index of the first particle of later calls (a shard of a larger set)
+    int particle0 = 0;
     // last forward
     bool have_tape = false;
-    int last_n = 0, last_iter = 0, last_hard = 0;
+    int last_n = 0, last_iter = 0, last_hard = 0, last_particle0 = 0;
     unsigned long long last_seed = 0;
     const float* last_theta = nullptr;
     int fwd_lanes = 0, adj_lanes = 0;
@@ -73,6 +76,10 @@ struct stamp_problem {
     int adj_mode = STAMP_ADJ_AUTO;
     float *pit_rel = nullptr, *pit_coef = nullptr;
     bool pit_ok = false;
+    // segment replay (checkpoint interval > 1): the per-substep states of the
+    // last forward, rebuilt in parallel, then swept at interval 1
+    float* full = nullptr;
+    bool replay_ok = false;
     // the bandwidth (pairwise distances + median) depends on theta only: the
     // solves run it on a second stream beside the rollouts
     bool overlap = true;
@@ -90,6 +97,9 @@ struct stamp_problem {
     unsigned *sk_hist = nullptr, *sk_sel = nullptr, *sk_counter = nullptr;
     int iters_run = 0;
     float best_hard = 0.f;
+    // test hook: the next Stein-direction launch's CTAs arm their first
+    // stage without issuing its copy and give up after a short wait
+    bool inject_wait_timeout = false;
     // kernel timing
     bool prof = false;
     unsigned prof_mask = ~0u;             // kernel kinds recorded while profiling
@@ -171,8 +181,18 @@ stamp_status check_dev(const void* ptr, const char* name, bool allow_null = fals
 // particles and breaks even near 4096, where the sequential teams fill the
 // GPU and the Jacobians' extra arithmetic no longer comes for free.
 bool time_parallel(const stamp_problem* p, int N) {
-    if (!p->pit_ok || p->adj_mode == STAMP_ADJ_SEQUENTIAL) return false;
+    if (!p->pit_ok || p->adj_mode == STAMP_ADJ_SEQUENTIAL || p->adj_mode == STAMP_ADJ_REPLAY)
+        return false;
     return p->adj_mode == STAMP_ADJ_TIME_PARALLEL || N <= kTimeParallelMaxN;
+}
+
+// The sweep a call with N particles runs: time-parallel (above), else the
+// segment replay where its scratch exists (checkpoint interval > 1) unless
+// the sequential sweep was asked for, else sequential.
+int adjoint_kind(const stamp_problem* p, int N) {
+    if (time_parallel(p, N)) return STAMP_ADJ_TIME_PARALLEL;
+    if (p->replay_ok && p->adj_mode != STAMP_ADJ_SEQUENTIAL) return STAMP_ADJ_REPLAY;
+    return STAMP_ADJ_SEQUENTIAL;
 }
 
 stamp_status fwd(stamp_problem* p, const float* theta, int N, unsigned long long seed, int iter,
@@ -182,11 +202,13 @@ stamp_status fwd(stamp_problem* p, const float* theta, int N, unsigned long long
     a.theta = theta; a.N = N; a.seed = seed; a.iter = iter; a.hard = hard;
     a.tape = p->tape; a.cost = cost; a.final_state = final_state; a.stats_min = stats_word;
     a.init_states = init_states;
+    a.particle0 = p->particle0;
     const int lanes = lanes_for(p, N, false);
     STAMP_TRY(timed(p, STAMP_K_ROLLOUT_FWD,
                     [&] { return stamp::launch_rollout_fwd(p->sc, a, lanes, p->stream); }));
     p->have_tape = true;
     p->last_n = N; p->last_seed = seed; p->last_iter = iter; p->last_hard = hard;
+    p->last_particle0 = p->particle0;
     p->last_theta = theta;
     return STAMP_OK;
 }
@@ -194,12 +216,25 @@ stamp_status fwd(stamp_problem* p, const float* theta, int N, unsigned long long
 stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
     stamp::RolloutArgs a{};
     a.theta = theta; a.N = N; a.seed = p->last_seed; a.iter = p->last_iter; a.hard = p->last_hard;
-    a.tape = p->tape; a.grad = grad; a.dropped = p->dropped;
-    if (time_parallel(p, N))
+    a.tape = p->tape; a.grad = grad; a.dropped = p->dropped; a.particle0 = p->last_particle0;
+    const int kind = adjoint_kind(p, N);
+    if (kind == STAMP_ADJ_TIME_PARALLEL)
         return timed(p, STAMP_K_ROLLOUT_ADJ, [&] {
             return stamp::launch_adjoint_time(p->sc, a, p->pit_rel, p->pit_coef, p->flag, p->stream);
         });
     const int lanes = lanes_for(p, N, true);
+    if (kind == STAMP_ADJ_REPLAY)
+        return timed(p, STAMP_K_ROLLOUT_ADJ, [&] {
+            cudaError_t e = stamp::launch_replay(p->sc, a, stamp::replay_lanes(p->sc.nb), p->full,
+                                                 p->stream);
+            if (e != cudaSuccess) return e;
+            SimConst sc1 = p->sc;          // the rebuilt tape has interval 1
+            sc1.C = 1;
+            sc1.n_ckpt = sc1.H * sc1.T;
+            stamp::RolloutArgs a1 = a;
+            a1.tape = p->full;
+            return stamp::launch_rollout_adj(sc1, a1, lanes, p->stream);
+        });
     return timed(p, STAMP_K_ROLLOUT_ADJ,
                  [&] { return stamp::launch_rollout_adj(p->sc, a, lanes, p->stream); });
 }
@@ -258,6 +293,11 @@ stamp_status svgd(stamp_problem* p, float* theta, const float* grad, int N, floa
         part = p->phi;
     } else if (!sgd_phase) {
         stamp::SvgdScratch s{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
+        if (p->inject_wait_timeout) {
+            s.wait_limit = kInjectedWaitLimit;
+            s.skip_first_copy = 1;
+            p->inject_wait_timeout = false;
+        }
         if (!bw_done) STAMP_TRY(bandwidth(p, theta, N, h_out, p->stream));
         STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
             return stamp::launch_phi(theta, grad, N, D, s, p->phi, stamp::kMaxShares, &shares,
@@ -463,6 +503,21 @@ cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lan
     return cudaErrorInvalidValue;
 }
 
+// The fewest lanes each block count supports: the replay is throughput
+// bound, and fewer lanes integrate the state less redundantly.
+int replay_lanes(int nb) { return nb == 1 ? 1 : nb == 2 ? 2 : 8; }
+
+cudaError_t launch_replay(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
+                          cudaStream_t st) {
+    switch (sc.nb) {
+        case 1: return launch_replay_nb1(sc, a, lanes, full, st);
+        case 2: return launch_replay_nb2(sc, a, lanes, full, st);
+        case 3: return launch_replay_nb3(sc, a, lanes, full, st);
+        case 4: return launch_replay_nb4(sc, a, lanes, full, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_rollout_adj(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st) {
     switch (sc.nb) {
         case 1: return launch_rollout_nb1(sc, a, lanes, true, st);
@@ -550,6 +605,8 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
     const size_t n = (size_t)max_particles;
     const size_t pit_coef_bytes = stamp::adjoint_time_coef_floats(max_particles, sc.H, sc.T) * sizeof(float);
     const bool pit = sc.nb == 1 && sc.C == 1 && pit_coef_bytes <= kMaxTimeParallelBytes;
+    const size_t full_bytes = (size_t)(sc.H * sc.T + 1) * n * sc.S * sizeof(float);
+    const bool replay = sc.C > 1 && full_bytes <= kMaxTimeParallelBytes;
     struct Part { void** dst; size_t bytes; };
     const Part parts[] = {
         {(void**)&p->tape, (size_t)(sc.n_ckpt + 1) * n * sc.S * sizeof(float)},
@@ -574,8 +631,10 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         {(void**)&p->wn, n * sizeof(float)},
         {(void**)&p->pit_rel, pit ? stamp::adjoint_time_rel_floats(max_particles, sc.H) * sizeof(float) : 0},
         {(void**)&p->pit_coef, pit ? pit_coef_bytes : 0},
+        {(void**)&p->full, replay ? full_bytes : 0},
     };
     p->pit_ok = pit;
+    p->replay_ok = replay;
     size_t total = 0;
     for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
     cudaError_t e = cudaMalloc(&p->arena, total);
@@ -694,6 +753,55 @@ stamp_status stamp_svgd_step(stamp_problem* p, float* theta, const float* grad_l
     return svgd(p, theta, grad_logp, N, adam_m, adam_v, step, lr, sgd_phase, h_out, phi_out);
 }
 
+stamp_status stamp_set_particle_offset(stamp_problem* p, int particle0) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    if (particle0 < 0) return fail(STAMP_EINVAL, "particle0 must be >= 0");
+    p->particle0 = particle0;
+    return STAMP_OK;
+}
+
+stamp_status stamp_svgd_step_rows(stamp_problem* p, const float* theta_all, const float* grad_all,
+                                  int N, int row0, int rows, float* theta_rows, float* adam_m,
+                                  float* adam_v, int step, float lr, int sgd_phase, float* h_out,
+                                  float* phi_out) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    STAMP_TRY(check_n(p, N));
+    if (row0 < 0 || rows < 1 || row0 + rows > N)
+        return fail(STAMP_EINVAL, "rows [%d, %d) outside [0, %d)", row0, row0 + rows, N);
+    STAMP_TRY(check_dev(theta_all, "theta_all"));
+    STAMP_TRY(check_dev(grad_all, "grad_all"));
+    STAMP_TRY(check_dev(theta_rows, "theta_rows"));
+    STAMP_TRY(check_dev(adam_m, "adam_m"));
+    STAMP_TRY(check_dev(adam_v, "adam_v"));
+    STAMP_TRY(check_dev(h_out, "h_out", true));
+    STAMP_TRY(check_dev(phi_out, "phi_out", true));
+    if (step < 1) return fail(STAMP_EINVAL, "step must be >= 1");
+    if ((reinterpret_cast<uintptr_t>(theta_all) | reinterpret_cast<uintptr_t>(grad_all)) & 15u)
+        return fail(STAMP_EINVAL, "theta_all and grad_all must be 16-byte aligned");
+    if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
+    if (p->kernel_kind != 0) return fail(STAMP_EINVAL, "row steps use the RBF kernel (kind 0)");
+    const int D = p->sc.D;
+    const float* part = grad_all + (size_t)row0 * D;   // SGD phase: phi = grad log rho
+    int shares = 1;
+    if (!sgd_phase) {
+        // the bandwidth from every particle (replicated on each shard), phi
+        // for this shard's rows, the sum over j split as for all N rows
+        stamp::SvgdScratch sc{p->d2, p->hist, p->sel, p->counter, p->h, p->flag};
+        STAMP_TRY(bandwidth(p, theta_all, N, h_out, p->stream));
+        STAMP_TRY(timed(p, STAMP_K_PHI, [&] {
+            return stamp::launch_phi_rows(theta_all, grad_all, N, D, row0, rows, sc, p->phi,
+                                          stamp::kMaxShares, &shares, p->stream);
+        }));
+        part = p->phi;
+    } else if (h_out) {
+        STAMP_CUDA(cudaMemcpyAsync(h_out, p->one, sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    }
+    return timed(p, STAMP_K_ADAM, [&] {
+        return stamp::launch_adam(theta_rows, part, shares, phi_out, adam_m, adam_v, rows * D, step,
+                                  lr, p->flag, p->stream);
+    });
+}
+
 stamp_status stamp_solve(stamp_problem* p, int N, int svgd_iters, int sgd_iters,
                          unsigned long long seed, float lr, const float* theta_init,
                          float* theta_out, float* cost_out, int k, int* topk_particle,
@@ -724,7 +832,8 @@ stamp_status stamp_solve_surrogate(stamp_problem* p, stamp_surrogate* s, int n_c
 
 stamp_status stamp_set_adjoint_mode(stamp_problem* p, int mode) {
     if (!p) return fail(STAMP_EINVAL, "NULL problem");
-    if (mode != STAMP_ADJ_SEQUENTIAL && mode != STAMP_ADJ_TIME_PARALLEL && mode != STAMP_ADJ_AUTO)
+    if (mode != STAMP_ADJ_SEQUENTIAL && mode != STAMP_ADJ_TIME_PARALLEL && mode != STAMP_ADJ_AUTO &&
+        mode != STAMP_ADJ_REPLAY)
         return fail(STAMP_EINVAL, "unknown adjoint mode %d", mode);
     p->adj_mode = mode;
     return STAMP_OK;
@@ -733,7 +842,7 @@ stamp_status stamp_set_adjoint_mode(stamp_problem* p, int mode) {
 stamp_status stamp_get_adjoint_mode(stamp_problem* p, int N, int* mode) {
     if (!p || !mode) return fail(STAMP_EINVAL, "NULL problem or mode");
     STAMP_TRY(check_n(p, N));
-    *mode = time_parallel(p, N) ? STAMP_ADJ_TIME_PARALLEL : STAMP_ADJ_SEQUENTIAL;
+    *mode = adjoint_kind(p, N);
     return STAMP_OK;
 }
 
@@ -796,6 +905,12 @@ stamp_status stamp_svgd_step_weighted(stamp_problem* p, float* theta, const floa
     if (!std::isfinite(lr)) return fail(STAMP_EINVAL, "lr is not finite");
     STAMP_CUDA(stamp::launch_dsvgd_weights(cost_relaxed, cost_hard, N, p->wn, p->stream));
     return svgd(p, theta, grad_logp, N, adam_m, adam_v, step, lr, 0, h_out, phi_out, p->wn);
+}
+
+stamp_status stamp_inject_wait_timeout(stamp_problem* p) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    p->inject_wait_timeout = true;
+    return STAMP_OK;
 }
 
 stamp_status stamp_set_target(stamp_problem* p, float target_cost, int check_every) {

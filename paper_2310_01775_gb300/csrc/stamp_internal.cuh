@@ -43,6 +43,7 @@ struct RolloutArgs {
     float* grad;            // N x D (adjoint): grad log rho = -dC/dtheta
     unsigned long long* dropped;   // count of particles whose reverse sweep overflowed
     const float* init_states;      // N x n_blocks x 3 initial poses (at rest), or NULL: the scene's
+    int particle0;          // global index of row 0 (Gumbel draws of a shard of a larger set)
 };
 
 // One problem instance of a batch, as the batched rollout kernels see it.
@@ -98,6 +99,17 @@ cudaError_t launch_rollout_adj(const SimConst& sc, const RolloutArgs& a, int lan
 bool lanes_supported(int nb, int lanes);
 int default_lanes(int nb, int N, bool adjoint);
 
+// Segment replay (rollout_nb*.cu): the states before every substep of the
+// last forward, rebuilt from its checkpoints for all (particle, segment)
+// pairs at once into `full` ([H*T + 1][N][S]); `lanes` per team.
+cudaError_t launch_replay(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
+                          cudaStream_t st);
+cudaError_t launch_replay_nb1(const SimConst&, const RolloutArgs&, int, float*, cudaStream_t);
+cudaError_t launch_replay_nb2(const SimConst&, const RolloutArgs&, int, float*, cudaStream_t);
+cudaError_t launch_replay_nb3(const SimConst&, const RolloutArgs&, int, float*, cudaStream_t);
+cudaError_t launch_replay_nb4(const SimConst&, const RolloutArgs&, int, float*, cudaStream_t);
+int replay_lanes(int nb);
+
 // Batched launchers (rollout_nb*.cu): cta threads per CTA, a multiple of 32.
 cudaError_t launch_rollout_batch(int nb, const SimConst& sc, const BatchArgs& b, int lanes, int cta,
                                  bool adjoint, cudaStream_t st);
@@ -128,6 +140,11 @@ struct SvgdScratch {
     unsigned* counter;    // 3 "last CTA" counters (zero between launches)
     float* h;             // bandwidth (device scalar)
     int* err;             // device error flags: 1 non-finite, 2 a bounded wait gave up
+    // Stein kernel's bounded waits: polls before a wait gives up (0: the
+    // library's default); skip_first_copy (a test hook) arms each CTA's first
+    // shared-memory stage without issuing its copy, so that wait runs out
+    unsigned wait_limit = 0;
+    int skip_first_copy = 0;
 };
 cudaError_t launch_pairwise(const float* theta, int N, int D, const SvgdScratch& s, cudaStream_t st);
 cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h_out,
@@ -138,6 +155,12 @@ cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h
 cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
                        float* part, int max_shares, int* shares, cudaStream_t st,
                        const float* wn = nullptr);
+// The same for rows [row0, row0 + rows) of phi only (sums over all N
+// particles, split into the same shares as for all rows; part holds
+// `*shares` blocks of rows x D).
+cudaError_t launch_phi_rows(const float* theta, const float* grad, int N, int D, int row0,
+                            int rows, const SvgdScratch& s, float* part, int max_shares, int* shares,
+                            cudaStream_t st, const float* wn = nullptr);
 // Structured kernel (svgd_struct.cu): C (N x 2H) offset/distance parameters and
 // S (N x M H) choice probabilities of each action; the Stein direction from
 // the raw bandwidths of C and S (h_plain, divided by H inside).

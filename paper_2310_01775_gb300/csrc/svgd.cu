@@ -263,14 +263,16 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
                                          const float* __restrict__ d2,
                                          const float* __restrict__ h_dev, float* __restrict__ part,
                                          int j_chunk, int* err, int rblock, int share,
-                                         const float* __restrict__ wn) {
+                                         const float* __restrict__ wn, unsigned wait_limit,
+                                         bool skip_first, int row0, int rows) {
     extern __shared__ __align__(128) float sm[];
     const int sf = phi_stage_floats(D, DP);
     // stage s: theta tile at sm + 2*s*sf, grad tile right after it
     float4* Ks = reinterpret_cast<float4*>(sm + 4 * sf);             // kW x kTJ
     uint64_t* bar = reinterpret_cast<uint64_t*>(Ks + kW * kTJ);       // 2 stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ib = (rblock * kW + warp) * kR;
+    // rows [row0, row0 + rows) of phi (all N: row0 = 0, rows = N)
+    const int ib = row0 + (rblock * kW + warp) * kR, re = row0 + rows;
     // this CTA's share of the sum over j: rows [jb, je) of theta and grad
     const int jb = share * j_chunk, je = min(N, jb + j_chunk);
     const int ntiles = (je - jb + kTJ - 1) / kTJ;
@@ -290,7 +292,7 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
         mbar_expect_tx(&bar[s], 2 * bulk);
         float* Ts = sm + 2 * s * sf;
         float* Gs = Ts + sf;
-        if (bulk) {
+        if (bulk && !(skip_first && t == 0)) {
             tma_load_1d(Ts, theta + (size_t)j0 * D, bulk, &bar[s]);
             tma_load_1d(Gs, grad + (size_t)j0 * D, bulk, &bar[s]);
         }
@@ -309,10 +311,10 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
 #pragma unroll
         for (int q = 0; q < DP; ++q) {
             const int d = lane + 32 * q;
-            ti[r][q] = (ib + r < N && d < D) ? theta[(size_t)(ib + r) * D + d] : 0.f;
+            ti[r][q] = (ib + r < re && d < D) ? theta[(size_t)(ib + r) * D + d] : 0.f;
             ag[r][q] = ar[r][q] = 0.f;
         }
-        dv[r] = (ib + r < N && jb + lane < je) ? d2[(size_t)(ib + r) * N + jb + lane] : 0.f;
+        dv[r] = (ib + r < re && jb + lane < je) ? d2[(size_t)(ib + r) * N + jb + lane] : 0.f;
     }
     unsigned phases = 0u;                       // bit s: parity of stage s
     for (int t = 0; t < ntiles; ++t) {
@@ -320,7 +322,7 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
         {
             float kv[kR];
 #pragma unroll
-            for (int r = 0; r < kR; ++r) kv[r] = (ib + r < N && lane < nj) ? expf(-dv[r] * inv_h) : 0.f;
+            for (int r = 0; r < kR; ++r) kv[r] = (ib + r < re && lane < nj) ? expf(-dv[r] * inv_h) : 0.f;
             if (wn) {   // Eq. dsvgd: k_ij scaled by w_j / w
                 const float wj = lane < nj ? wn[j0 + lane] : 0.f;
 #pragma unroll
@@ -331,22 +333,22 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
         if (t + 1 < ntiles) {   // next tile's distances, consumed one iteration later
             const int jn = j0 + kTJ + lane;
 #pragma unroll
-            for (int r = 0; r < kR; ++r) dv[r] = (ib + r < N && jn < je) ? d2[(size_t)(ib + r) * N + jn] : 0.f;
+            for (int r = 0; r < kR; ++r) dv[r] = (ib + r < re && jn < je) ? d2[(size_t)(ib + r) * N + jn] : 0.f;
         }
         const unsigned par = (phases >> s) & 1u;
         unsigned spins = 0;
-        while (!mbar_try_wait(&bar[s], par) && ++spins < kWaitLimit) {
+        while (!mbar_try_wait(&bar[s], par) && ++spins < wait_limit) {
         }
-        if (__syncthreads_or(spins >= kWaitLimit)) {   // a copy never landed: report, stop
+        if (__syncthreads_or(spins >= wait_limit)) {   // a copy never landed: report, stop
             if (tid == 0) {
                 atomicOr(err, 2);
                 // a last bounded wait for the copies still in flight (this
                 // stage and, if issued, the next) before the CTA exits
-                for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&bar[s], par); ++w) {
+                for (unsigned w = 0; w < wait_limit && !mbar_try_wait(&bar[s], par); ++w) {
                 }
                 const unsigned pn = (phases >> (s ^ 1)) & 1u;
                 if (t + 1 < ntiles)
-                    for (unsigned w = 0; w < kWaitLimit && !mbar_try_wait(&bar[s ^ 1], pn); ++w) {
+                    for (unsigned w = 0; w < wait_limit && !mbar_try_wait(&bar[s ^ 1], pn); ++w) {
                     }
             }
             return;
@@ -376,14 +378,14 @@ __device__ __forceinline__ void phi_body(const float* __restrict__ theta,
     }
     // partial phi of this j-share; the Adam kernel sums the shares in order
     const float inv_n = wn ? 1.f : 1.f / (float)N, two_h = 2.f * inv_h;
-    float* out = part + (size_t)share * N * D;
+    float* out = part + (size_t)share * rows * D;
 #pragma unroll
     for (int r = 0; r < kR; ++r)
 #pragma unroll
         for (int q = 0; q < DP; ++q) {
             const int d = lane + 32 * q;
-            if (ib + r < N && d < D)
-                out[(size_t)(ib + r) * D + d] = (ag[r][q] + two_h * ar[r][q]) * inv_n;
+            if (ib + r < re && d < D)
+                out[(size_t)(ib - row0 + r) * D + d] = (ag[r][q] + two_h * ar[r][q]) * inv_n;
         }
 }
 
@@ -393,8 +395,11 @@ __global__ void __launch_bounds__(kW * 32) phi_kernel(const float* __restrict__ 
                                                       const float* __restrict__ d2,
                                                       const float* __restrict__ h_dev,
                                                       float* __restrict__ part, int j_chunk,
-                                                      int* err, const float* __restrict__ wn) {
-    phi_body<DP>(theta, grad, N, D, d2, h_dev, part, j_chunk, err, blockIdx.x, blockIdx.y, wn);
+                                                      int* err, const float* __restrict__ wn,
+                                                      unsigned wait_limit, int skip_first, int row0,
+                                                      int rows) {
+    phi_body<DP>(theta, grad, N, D, d2, h_dev, part, j_chunk, err, blockIdx.x, blockIdx.y, wn,
+                 wait_limit, skip_first != 0, row0, rows);
 }
 
 // Batched: work item (instance, row block, j-share); DP covers the batch's largest D.
@@ -406,7 +411,8 @@ __global__ void __launch_bounds__(kW * 32) phi_batch_kernel(const SvgdInst* __re
     const int4 it = items[blockIdx.x];
     const SvgdInst& g = inst[it.x];
     if (!active[g.gid]) return;
-    phi_body<DP>(g.theta, g.grad, g.N, g.D, g.d2, g.h, g.part, g.j_chunk, err, it.y, it.z, nullptr);
+    phi_body<DP>(g.theta, g.grad, g.N, g.D, g.d2, g.h, g.part, g.j_chunk, err, it.y, it.z, nullptr,
+                 kWaitLimit, false, 0, g.N);
 }
 
 // Adam (Kingma & Ba 2015) with gradient -phi, phi the in-order sum of the
@@ -564,7 +570,8 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ th
 template <int DP>
 cudaError_t phi_launch(const float* theta, const float* grad, int N, int D, const float* d2,
                        const float* h_dev, float* part, int shares, int j_chunk, int* err,
-                       const float* wn, cudaStream_t st) {
+                       const float* wn, unsigned wait_limit, int skip_first, int row0, int rows,
+                       cudaStream_t st) {
     const size_t smem = (size_t)4 * phi_stage_floats(D, DP) * sizeof(float) +
                         (size_t)kW * kTJ * sizeof(float4) + 2 * sizeof(uint64_t);
     if (smem > 48 * 1024) {
@@ -572,9 +579,9 @@ cudaError_t phi_launch(const float* theta, const float* grad, int N, int D, cons
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int rows = kW * kR;
-    phi_kernel<DP><<<dim3((N + rows - 1) / rows, shares), kW * 32, smem, st>>>(
-        theta, grad, N, D, d2, h_dev, part, j_chunk, err, wn);
+    const int per_cta = kW * kR;
+    phi_kernel<DP><<<dim3((rows + per_cta - 1) / per_cta, shares), kW * 32, smem, st>>>(
+        theta, grad, N, D, d2, h_dev, part, j_chunk, err, wn, wait_limit, skip_first, row0, rows);
     return cudaGetLastError();
 }
 
@@ -604,8 +611,9 @@ cudaError_t launch_median_digit(int N, int digit, const SvgdScratch& s, float* h
     return cudaGetLastError();
 }
 
-cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
-                       float* part, int max_shares, int* shares, cudaStream_t st, const float* wn) {
+cudaError_t launch_phi_rows(const float* theta, const float* grad, int N, int D, int row0,
+                            int rows, const SvgdScratch& s, float* part, int max_shares, int* shares,
+                            cudaStream_t st, const float* wn) {
     // TMA bulk copies need 16-byte aligned sources
     if ((reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(grad)) & 15u)
         return cudaErrorMisalignedAddress;
@@ -616,18 +624,24 @@ cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, cons
     want = want < 1 ? 1 : (want > max_shares ? max_shares : want);
     const int j_chunk = ((N + want - 1) / want + kTJ - 1) / kTJ * kTJ;
     *shares = (N + j_chunk - 1) / j_chunk;
+    const unsigned limit = s.wait_limit ? s.wait_limit : kWaitLimit;
     const int dp = (D + 31) / 32;
     switch (dp) {
-        case 1: return phi_launch<1>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
-        case 2: return phi_launch<2>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
-        case 3: return phi_launch<3>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
-        case 4: return phi_launch<4>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
+        case 1: return phi_launch<1>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, limit, s.skip_first_copy, row0, rows, st);
+        case 2: return phi_launch<2>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, limit, s.skip_first_copy, row0, rows, st);
+        case 3: return phi_launch<3>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, limit, s.skip_first_copy, row0, rows, st);
+        case 4: return phi_launch<4>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, limit, s.skip_first_copy, row0, rows, st);
         case 5: case 6:
-            return phi_launch<6>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
+            return phi_launch<6>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, limit, s.skip_first_copy, row0, rows, st);
         case 7: case 8: case 9:
-            return phi_launch<9>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, st);
+            return phi_launch<9>(theta, grad, N, D, s.d2, s.h, part, *shares, j_chunk, s.err, wn, limit, s.skip_first_copy, row0, rows, st);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_phi(const float* theta, const float* grad, int N, int D, const SvgdScratch& s,
+                       float* part, int max_shares, int* shares, cudaStream_t st, const float* wn) {
+    return launch_phi_rows(theta, grad, N, D, 0, N, s, part, max_shares, shares, st, wn);
 }
 
 cudaError_t launch_adam(float* theta, const float* part, int shares, float* phi_out, float* m,

@@ -21,7 +21,7 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 STAMP_OK, STAMP_EINVAL, STAMP_ENOMEM, STAMP_ECUDA, STAMP_ENONFINITE, STAMP_ETIMEOUT = range(6)
-STAMP_ADJ_SEQUENTIAL, STAMP_ADJ_TIME_PARALLEL, STAMP_ADJ_AUTO = 0, 1, 2
+STAMP_ADJ_SEQUENTIAL, STAMP_ADJ_TIME_PARALLEL, STAMP_ADJ_AUTO, STAMP_ADJ_REPLAY = 0, 1, 2, 3
 KERNELS = ("rollout_fwd", "rollout_adj", "pairwise", "median", "phi", "adam", "topk", "init",
            "surrogate", "screen")
 STAMP_NKERNELS = len(KERNELS)
@@ -102,6 +102,9 @@ _sigs = {
     "stamp_batch_read_theta": [_vp, _i, _vp],
     "stamp_solve_info": [_vp, _vp, _vp],
     "stamp_fp32_fma_peak": [_i, _vp, _vp],
+    "stamp_inject_wait_timeout": [_vp],
+    "stamp_set_particle_offset": [_vp, _i],
+    "stamp_svgd_step_rows": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _f, _i, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -317,7 +320,8 @@ class Problem:
         _check(_lib.stamp_set_overlap(self.handle, int(enable)))
 
     def set_adjoint_mode(self, mode):
-        """STAMP_ADJ_AUTO (default), STAMP_ADJ_TIME_PARALLEL or STAMP_ADJ_SEQUENTIAL."""
+        """STAMP_ADJ_AUTO (default), STAMP_ADJ_TIME_PARALLEL, STAMP_ADJ_REPLAY or
+        STAMP_ADJ_SEQUENTIAL."""
         _check(_lib.stamp_set_adjoint_mode(self.handle, int(mode)))
 
     def adjoint_mode(self, N):
@@ -328,11 +332,30 @@ class Problem:
 
     def adjoint_launches(self, N):
         """Kernel launches of one reverse sweep with N particles (the
-        time-parallel sweep: relaxed parameters, Jacobians, recurrence)."""
-        return {STAMP_ADJ_TIME_PARALLEL: 3}.get(self.adjoint_mode(N), 1)
+        time-parallel sweep: relaxed parameters, Jacobians, recurrence; the
+        replay: rebuild, sweep)."""
+        return {STAMP_ADJ_TIME_PARALLEL: 3, STAMP_ADJ_REPLAY: 2}.get(self.adjoint_mode(N), 1)
 
     def set_lanes(self, fwd_lanes, adj_lanes):
         stamp_set_lanes(self.handle, fwd_lanes, adj_lanes)
+
+    def set_particle_offset(self, particle0):
+        """Later rollouts' row r is particle particle0 + r of a larger set."""
+        _check(_lib.stamp_set_particle_offset(self.handle, int(particle0)))
+
+    def svgd_step_rows(self, theta_all, grad_all, N, row0, rows, theta_rows, adam_m, adam_v, step,
+                       lr, sgd_phase=0, h_out=None, phi_out=None):
+        """The Stein step of rows [row0, row0 + rows) from the gathered particles."""
+        _check(_lib.stamp_svgd_step_rows(self.handle, _f32(theta_all, "theta_all"),
+                                         _f32(grad_all, "grad_all"), N, row0, rows,
+                                         _f32(theta_rows, "theta_rows"), _f32(adam_m, "adam_m"),
+                                         _f32(adam_v, "adam_v"), step, lr, int(sgd_phase),
+                                         _f32(h_out, "h_out"), _f32(phi_out, "phi_out")))
+
+    def inject_wait_timeout(self):
+        """Test hook: the next Stein-direction launch's first copy is never
+        issued and its bounded wait runs out (STAMP_ETIMEOUT at the next sync)."""
+        _check(_lib.stamp_inject_wait_timeout(self.handle))
 
     def dropped_gradients(self):
         return stamp_dropped_gradients(self.handle)

@@ -42,11 +42,12 @@ class Reference:
             self.floor_grad = rel_err(g32, self.grad)
             self.ok &= self.floor_grad < GRAD_TOL / 10
 
-    def check(self, tape, final, cost, grad=None, min_frac=0.3):
-        """Bar on conditioned particles; on all particles the GPU's error
-        distribution must match the float32 floor's."""
+    def check(self, tape, final, cost, grad=None, min_frac=0.3, min_count=3):
+        """Bar on conditioned particles (at least min_count of them and a
+        min_frac share); on all particles the GPU's error distribution must
+        match the float32 floor's."""
         ok = self.ok
-        need = min(3, len(ok)) if min_frac > 0 else 0
+        need = min(min_count, len(ok)) if min_frac > 0 else 0
         assert ok.sum() >= need and ok.mean() >= min_frac, \
             f"only {ok.sum()} of {len(ok)} particles conditioned"
         et = rel_err(tape, self.traj)

@@ -121,3 +121,37 @@ def test_mlp_training_fits_a_teacher_network():
     net.close()
     assert np.isfinite(losses).all()
     assert losses[-1] < 0.2 * losses[0], losses
+
+
+def test_weight_gradients_and_training_are_reproducible():
+    """The weight gradients run on the tensor cores per row split and are
+    summed over the splits in a fixed order (no atomics): two backward passes
+    give the same bits, and so do two trainings from the same start."""
+    from paper_2310_01775_gb300 import stamp as S
+    rows = 3000                                      # 24 tiles: several row splits
+    params = torch.tensor(packed(W.mlp_init(SIZES, 13)), device="cuda")
+    rng = np.random.default_rng(7)
+    x = torch.tensor(rng.uniform(-1, 1, size=(rows, IN)), dtype=torch.float32, device="cuda")
+    dy = torch.tensor(rng.standard_normal((rows, OUT)), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    net = S.MLP(IN, OUT, rows, rows, stream)
+    net.set_params(params)
+    y = torch.empty(rows, OUT, device="cuda")
+    dps = []
+    for _ in range(2):
+        dp = torch.empty(net.n_params, device="cuda")
+        net.forward_saved(x, rows, y, 0)
+        net.backward(dy, rows, 0, None, dp)
+        dps.append(dp)
+    net.sync()
+    net.close()
+    assert torch.equal(dps[0], dps[1])
+    t = torch.tensor(rng.uniform(-1, 1, size=(rows, OUT)), dtype=torch.float32, device="cuda")
+    outs = []
+    for _ in range(2):
+        p = params.clone()
+        net = S.MLP(IN, OUT, 1000, 1000, stream)
+        net.train(p, x, t, rows, 2, 1000, 1e-3)
+        net.close()
+        outs.append(p)
+    assert torch.equal(outs[0], outs[1])
