@@ -36,7 +36,7 @@ N_OFF, N_DIST = 11, 16
 MODE_COST = 1e-2
 POLISH_BELOW = 5e-2          # grid costs in [MODE_COST, POLISH_BELOW) are polished
 DESCENT, SPREAD = 0.7, 2.0
-N_PARTICLES, ITERS, SGD_ITERS = 128, 200, 100
+N_PARTICLES, ITERS, SGD_ITERS = 128, 200, 200
 
 
 def params():

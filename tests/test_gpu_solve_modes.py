@@ -1,4 +1,4 @@
-"""Whole-solve pin on the GPU: stamp_solve (Algorithm 1: 200 SVGD then 100
+"""Whole-solve pin on the GPU: stamp_solve (Algorithm 1: 200 SVGD then 200
 SGD iterations, N = 128) on the planted two-push problems of
 tests/test_oracle_solve_modes.py must pass the same brute-force pin as the
 FP64 oracle's solve: every mode held by a final particle's discrete plan,

@@ -4,7 +4,7 @@ Two planted two-push problems (goal = end pose of a random hard plan, so a
 zero-pose-error plan exists).  Brute force over the 16 side sequences x a
 grid of offsets and distances per push (then an FP64 gradient polish near
 the bar) gives the modes: side sequences that reach hard cost < 1e-2.  The
-oracle's solve (N = 128 particles, 200 SVGD then 100 SGD iterations of
+oracle's solve (N = 128 particles, 200 SVGD then 200 SGD iterations of
 Algorithm 1) must hold every mode
 among its final particles' discrete plans, move downhill (term A of
 Eq. svgd), spread its particles (term B) and end with its best particle on a
