@@ -9,8 +9,8 @@
 // once in a CUDA graph and replayed.  The iteration number and Adam's step
 // live on the device, so the replayed launches see them advance.  Every
 // instance computes exactly what stamp_solve computes for it alone with the
-// same lanes and checkpoint interval (same kernels, same Stein-sum split,
-// same bias-correction constants).
+// same lanes, checkpoint interval and the sequential reverse sweep (same
+// kernels, same Stein-sum split, same bias-correction constants).
 #include <algorithm>
 #include <chrono>
 #include <cstdarg>

@@ -2,8 +2,9 @@
 
 The batch runs the same kernels as a single problem, with per-instance
 constants and buffers, so every instance must come out bit for bit as the
-same instance solved alone by stamp_solve with the same lanes and checkpoint
-interval: particles, hard costs and top-3.  The single-problem path is itself
+same instance solved alone by stamp_solve with the same lanes, checkpoint
+interval and reverse sweep (the sequential one): particles, hard costs and
+top-3.  The single-problem path is itself
 parity-tested against the FP64 oracle.  Graph replay must equal direct
 launches; early stop must freeze exactly the instances that met the target.
 """
@@ -54,6 +55,9 @@ def test_batch_equals_individual_solves_bitwise():
         P = dict(W.PHYSICS, n_blocks=d["n_blocks"], H=d["H"], T=T, ckpt_every=k)
         prob = S.Problem(P, d["init"], d["goal"], d["N"], torch.cuda.current_stream().cuda_stream)
         prob.set_lanes(l, l)
+        # the batch's reverse sweep is the sequential one (segment recompute
+        # on the team's serial path at C > 1)
+        prob.set_adjoint_mode(S.STAMP_ADJ_SEQUENTIAL)
         th = torch.empty(d["N"], prob.D, device="cuda")
         cost = torch.empty(d["N"], device="cuda")
         top = np.zeros(3, dtype=np.int32)
@@ -133,4 +137,71 @@ def test_autotune_picks_supported_configs_and_solves():
         b.set_config(1, 3, 64, 25)          # unsupported lane count
     with pytest.raises(S.StampError):
         b.set_config(2, 8, 64, 7)           # does not divide T
+    b.close()
+
+
+SOFT = dict(k_contact=1e3, c_contact=10.0)
+
+
+def test_batched_iterations_match_the_oracle_for_every_block_count():
+    """The batched kernels against the FP64 oracle directly: one instance of
+    each block-count class (ragged particle counts), three Algorithm 1
+    iterations with the softer contact (every rollout well-conditioned);
+    the particles after them and the final hard costs against the oracle's
+    own loop on the same seeded inputs."""
+    from oracle import stamp_oracle as O
+    S = _S()
+    T, iters, lr = 50, 3, 1e-2
+    shapes = [(1, 2, 37), (2, 2, 33), (3, 2, 20), (4, 2, 12)]
+    insts = []
+    for g, (nb, H, N) in enumerate(shapes):
+        p = dict(W.PHYSICS, SOFT, n_blocks=nb, H=H, T=T)
+        init, goal = W.scene(p, 60 + g)
+        insts.append({"n_blocks": nb, "H": H, "N": N, "seed": 2000 + g, "init": init, "goal": goal})
+    b = S.Batch(dict(W.PHYSICS, SOFT, T=T), insts, torch.cuda.current_stream().cuda_stream)
+    for nb, (l, c, k) in CONFIG.items():
+        b.set_config(nb, l, c, k)
+    b.solve(iters, lr, use_graph=True)
+    res = b.results()
+    for g, d in enumerate(insts):
+        P = dict(W.PHYSICS, SOFT, n_blocks=d["n_blocks"], H=d["H"], T=T, ckpt_every=25)
+        init = np.asarray(d["init"], dtype=np.float32).astype(np.float64)
+        goal = np.asarray(d["goal"], dtype=np.float32).astype(np.float64)
+        ref = O.solve(P, init, goal, d["N"], iters, 0, d["seed"], lr, k=0)
+        D = d["H"] * (4 * d["n_blocks"] + 2)
+        got = torch.empty(d["N"], D, device="cuda")
+        b.read_theta(g, got)
+        err = np.abs(got.cpu().numpy() - ref["theta"])
+        assert err.max() <= 1e-4, (g, float(err.max()))
+        c_ref = float(ref["cost_hard"].min())
+        assert abs(res["best_cost"][g] - c_ref) <= 1e-4 * max(c_ref, 1e-6) + 1e-7, (g, res["best_cost"][g], c_ref)
+    b.close()
+
+
+def test_batched_plan_sets_match_the_oracle():
+    """The soft-contact whole-solve case of stamp_solve (1 block, H = 2,
+    T = 50, N = 32, 200 iterations; four seeds) run as one batch: each
+    instance's top-3 discrete plan set equals the FP64 oracle's (stored by
+    tests/golden/make_solve_golden.py)."""
+    import json
+    import os
+    from oracle import stamp_oracle as O
+    S = _S()
+    P = W.params("pusher1_h2", **SOFT)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "solve_pusher1_h2_soft.json")) as f:
+        gold = json.load(f)["seeds"]
+    insts = []
+    for seed in range(4):
+        init, goal = W.scene(P, seed)
+        insts.append({"n_blocks": 1, "H": P["H"], "N": P["N"], "seed": seed, "init": init, "goal": goal})
+    b = S.Batch(dict(P), insts, torch.cuda.current_stream().cuda_stream)
+    b.set_config(1, 4, 64, P["ckpt_every"])
+    b.solve(P["svgd_iters"], P["lr"], use_graph=True)
+    res = b.results()
+    for seed in range(4):
+        th = torch.empty(P["N"], O.dims(P)[2], device="cuda")
+        b.read_theta(seed, th)
+        th = th.cpu().numpy()
+        plans = {tuple(int(x) for x in O.plan_codes(th[i:i + 1], P)[0]) for i in res["top3"][seed] if i >= 0}
+        assert plans == {tuple(p) for p in gold[str(seed)]["f64"]["topk_plans"]}, seed
     b.close()
