@@ -4,8 +4,8 @@
 // a warp that cooperate on one particle.
 //
 // Work split inside a team of L lanes: the M*NB (pusher, block) contact items
-// and the 8 corner tests of every block pair are dealt round-robin to the
-// lanes; every lane runs the same instruction stream (items only change the
+// (pushers on their own object first) and the 8 corner tests of every block
+// pair are dealt round-robin to the lanes; every lane runs the same instruction stream (items only change the
 // data, never the control flow), the per-block forces are summed with an xor
 // butterfly (identical sums on every lane), and every lane then integrates
 // the full state redundantly.  Particle state lives in registers for the
@@ -97,6 +97,25 @@ __device__ __forceinline__ void yaw_sincos(float x, float* s, float* c) { sincos
 __device__ __forceinline__ void side_normal(int s, float& nx, float& ny) {
     nx = (s == 1) ? 1.f : (s == 3) ? -1.f : 0.f;
     ny = (s == 0) ? 1.f : (s == 2) ? -1.f : 0.f;
+}
+
+// Item e of the M*NB (pusher, block) pairs: first the M pairs of a pusher
+// and its own object (the block it is placed against: in contact through
+// most of the push), then the pairs of a pusher and another block (in
+// contact only where blocks meet).  Dealt round-robin to the lanes, the
+// nearly-always-active contacts land one per lane (up to M lanes), so no
+// lane's serial path carries more of them than the team width forces.
+template <int NB>
+__device__ __forceinline__ void item_of(int e, int& c, int& b) {
+    constexpr int M = Dims<NB>::M;
+    if (NB == 1 || e < M) {
+        c = e;
+        b = e / 4;
+        return;
+    }
+    const int r = e - M, k = r % (NB > 1 ? NB - 1 : 1);
+    c = r / (NB > 1 ? NB - 1 : 1);
+    b = k < c / 4 ? k : k + 1;
 }
 
 // Per-lane (pusher, block) item slots of the current action.
@@ -198,9 +217,10 @@ __device__ __forceinline__ void make_slots(const SimConst& sc, const Blocks<NB>&
     for (int q = 0; q < Slots<NB, L>::SP; ++q) {
         const int e = lane + q * L;
         const bool on = e < Dims<NB>::NPI;
-        const int c = on ? e / NB : 0;
+        int c = 0, b = 0;
+        if (on) item_of<NB>(e, c, b);
         sl.c[q] = on ? c : -1;
-        sl.b[q] = e % NB;
+        sl.b[q] = b;
         const int o = c / 4, side = c % 4;
         float nx, ny;
         side_normal(side, nx, ny);

@@ -155,16 +155,16 @@ def test_batched_iterations_match_the_oracle_for_every_block_count():
     shapes = [(1, 2, 37), (2, 2, 33), (3, 2, 20), (4, 2, 12)]
     insts = []
     for g, (nb, H, N) in enumerate(shapes):
-        p = dict(W.PHYSICS, SOFT, n_blocks=nb, H=H, T=T)
+        p = dict(W.PHYSICS, **SOFT, n_blocks=nb, H=H, T=T)
         init, goal = W.scene(p, 60 + g)
         insts.append({"n_blocks": nb, "H": H, "N": N, "seed": 2000 + g, "init": init, "goal": goal})
-    b = S.Batch(dict(W.PHYSICS, SOFT, T=T), insts, torch.cuda.current_stream().cuda_stream)
+    b = S.Batch(dict(W.PHYSICS, **SOFT, T=T), insts, torch.cuda.current_stream().cuda_stream)
     for nb, (l, c, k) in CONFIG.items():
         b.set_config(nb, l, c, k)
     b.solve(iters, lr, use_graph=True)
     res = b.results()
     for g, d in enumerate(insts):
-        P = dict(W.PHYSICS, SOFT, n_blocks=d["n_blocks"], H=d["H"], T=T, ckpt_every=25)
+        P = dict(W.PHYSICS, **SOFT, n_blocks=d["n_blocks"], H=d["H"], T=T, ckpt_every=25)
         init = np.asarray(d["init"], dtype=np.float32).astype(np.float64)
         goal = np.asarray(d["goal"], dtype=np.float32).astype(np.float64)
         ref = O.solve(P, init, goal, d["N"], iters, 0, d["seed"], lr, k=0)
