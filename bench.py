@@ -197,12 +197,14 @@ def surrogate_vs_plain(stream, seeds=(3, 4, 5)):
             "time_to_plain_final_cost": match}
 
 
-def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3, check_every=10):
+def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3, check_every=10,
+                    screen=True):
     """256 seeded uneven instances (1-4 blocks, H 2-8, N log-uniform 64-1024,
     T=100; goals planted: the end poses of a hard rollout of a random plan)
     solved together: autotuned launch configuration, graph-replayed
     iterations, per-instance early stop at the target (hard simulator check
-    every 10 iterations), at most 500 iterations."""
+    every 10 iterations), at most 500 iterations; then the same batch with
+    surrogate screening (batched_screened)."""
     import torch
     from paper_2310_01775_gb300 import stamp as S
     from paper_2310_01775_gb300 import workloads as W
@@ -236,6 +238,7 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
     done = np.where(stopped, r["seconds_to_target"], r["seconds"])
     b.close()
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
+    screened = batched_screened(insts, cfg, stream, iters, target, check_every, stopped) if screen else None
     return {"instances": n, "particles": int(sum(d["N"] for d in insts)),
             "units_per_iteration_all_active": int(sum(d["N"] * d["H"] * 100 for d in insts)),
             "value": r["units"] / r["seconds"], "unit": UNIT, "seconds": r["seconds"],
@@ -248,7 +251,52 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
             "median_iterations": float(np.median(r["iterations"])),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "over": "the whole solve (all kernels, checks included)",
-                         "peak_source": peak_src}}
+                         "peak_source": peak_src},
+            "surrogate_screened": screened}
+
+
+def batched_screened(insts, cfg, stream, iters, target, check_every, plain_stopped, factor=64):
+    """The same batch with surrogate screening: one surrogate per block count
+    of 1-3 (trained on 2^20 simulator transitions of T=100 pushes; horizon up
+    to 8), each instance of 1-3 blocks starting from the N of 64 N draws of
+    lowest surrogate cost (4-block instances, which no surrogate models,
+    start from their plain draws); same launch configuration, iterations,
+    target and checks as the plain batch."""
+    from paper_2310_01775_gb300 import stamp as S
+    from paper_2310_01775_gb300 import surrogate_compare as SC
+    from paper_2310_01775_gb300 import workloads as W
+    max_n = max(d["N"] for d in insts)
+    surs, train_s = {}, 0.0
+    for nb in (1, 2, 3):
+        P = dict(W.PHYSICS, n_blocks=nb, H=8, T=100, ckpt_every=25)
+        surs[nb], secs, _ = SC.train_surrogate(P, 1 << 20, stream, factor * max_n, max_n)
+        train_s += secs
+    b = S.Batch(dict(W.PHYSICS, T=100), insts, stream)
+    for nb, c in cfg.items():
+        b.set_config(int(nb), c["lanes"], c["cta"], c["ckpt_every"])
+    t0 = time.perf_counter()
+    for g, d in enumerate(insts):
+        if d["n_blocks"] in surs:
+            b.screen(surs[d["n_blocks"]], g, factor * d["N"])
+    screen_s = time.perf_counter() - t0
+    b.solve(iters, 1e-2, target, check_every, True)
+    r = b.results()
+    b.close()
+    for sur in surs.values():
+        sur.close()
+    stopped = r["seconds_to_target"] >= 0
+    tts = np.sort(r["seconds_to_target"][stopped] + screen_s)
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
+    both = stopped & plain_stopped
+    return {"reached": int(stopped.sum()), "reached_by_block_count": {
+                str(nb): f"{int(sum(stopped[g] for g, d in enumerate(insts) if d['n_blocks'] == nb))}"
+                         f"/{sum(1 for d in insts if d['n_blocks'] == nb)}" for nb in range(1, 5)},
+            "reached_by_both_arms": int(both.sum()),
+            "seconds": r["seconds"], "screening_seconds": round(screen_s, 3),
+            "surrogate_training_seconds": round(train_s, 3),
+            "time_to_solution_s": {"p50": pct(tts, 50), "p99": pct(tts, 99),
+                                   "over": "instances that reached the target, screening included"},
+            "median_iterations": float(np.median(r["iterations"]))}
 
 
 def workload_config(args, P):

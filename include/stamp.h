@@ -553,6 +553,16 @@ stamp_status stamp_batch_results(stamp_batch* batch, int* iterations, float* bes
                                  double* seconds);
 /* Copy one instance's particles (N x D) to host or device memory. */
 stamp_status stamp_batch_read_theta(stamp_batch* batch, int instance, float* theta_out);
+/* Surrogate screening for a batched instance (the surrogate-assisted solve's
+ * first step, for serving): draw n_candidates particles theta ~ U(-1,1)^D
+ * from the instance's seed (the draws stamp_solve_surrogate makes), keep the
+ * N of lowest noise-free surrogate cost (ties to the lower index) and start
+ * the instance's next stamp_batch_solve from them instead of its first N
+ * draws.  The surrogate must model the instance's block count and a horizon
+ * >= its H; N <= 4096, N <= n_candidates <= the surrogate's max_rows.  Runs
+ * on the surrogate's stream and waits for it. */
+stamp_status stamp_batch_screen(stamp_batch* batch, stamp_surrogate* surrogate, int instance,
+                                int n_candidates);
 
 /* Static text of a status code, and the last error message of this thread. */
 const char* stamp_status_str(stamp_status s);

@@ -126,6 +126,8 @@ struct stamp_batch {
     int graph_iters = 0;
     float graph_lr = 0.f;
     bool graph_dirty = true;
+    // instances whose next solve starts from particles set by stamp_batch_screen
+    std::vector<char> screened;
     // last solve
     std::vector<int> iters_done;
     std::vector<float> best;
@@ -305,6 +307,7 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
     }
     stamp_batch* b = new stamp_batch();
     b->n = n_instances;
+    b->screened.assign(n_instances, 0);
     b->phys = phys;
     b->inst.assign(inst, inst + n_instances);
     b->user = static_cast<cudaStream_t>(cuda_stream);
@@ -509,7 +512,10 @@ stamp_status stamp_batch_autotune(stamp_batch* b, int reps) {
     if (reps < 1) reps = 1;
     B_CUDA(cudaStreamSynchronize(b->user));
     for (int g = 0; g < b->n; ++g)
-        B_CUDA(stamp::launch_init_theta(b->theta + b->elem0[g], b->inst[g].N, b->D[g], b->inst[g].seed, b->st));
+        if (!b->screened[g])
+            B_CUDA(stamp::launch_init_theta(b->theta + b->elem0[g], b->inst[g].N, b->D[g],
+                                            b->inst[g].seed, b->st));
+    b->screened.assign(b->n, 0);
     std::vector<int> ones(b->n, 1);
     B_CUDA(cudaMemcpyAsync(b->active, ones.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->st));
     B_CUDA(cudaMemsetAsync(b->iter, 0, sizeof(int), b->st));
@@ -577,7 +583,10 @@ stamp_status stamp_batch_solve(stamp_batch* b, int iters, float lr, float target
     const auto t_start = std::chrono::steady_clock::now();
     b->lr = lr;
     for (int g = 0; g < b->n; ++g)
-        B_CUDA(stamp::launch_init_theta(b->theta + b->elem0[g], b->inst[g].N, b->D[g], b->inst[g].seed, b->st));
+        if (!b->screened[g])
+            B_CUDA(stamp::launch_init_theta(b->theta + b->elem0[g], b->inst[g].N, b->D[g],
+                                            b->inst[g].seed, b->st));
+    b->screened.assign(b->n, 0);
     B_CUDA(cudaMemsetAsync(b->m, 0, b->n_elem * 4, b->st));
     B_CUDA(cudaMemsetAsync(b->v, 0, b->n_elem * 4, b->st));
     B_CUDA(cudaMemsetAsync(b->iter, 0, sizeof(int), b->st));
@@ -643,6 +652,37 @@ stamp_status stamp_batch_solve(stamp_batch* b, int iters, float lr, float target
     for (int g = 0; g < b->n; ++g) b->best[g] = mins[g];
     if (flag & 2) return bfail(STAMP_ETIMEOUT, "a bounded device wait gave up");
     if (flag & 1) return bfail(STAMP_ENONFINITE, "a non-finite particle or Stein direction was produced");
+    return STAMP_OK;
+}
+
+stamp_status stamp_batch_screen(stamp_batch* b, stamp_surrogate* s, int g, int n_candidates) {
+    if (!b || !s) return bfail(STAMP_EINVAL, "NULL batch or surrogate");
+    if (g < 0 || g >= b->n) return bfail(STAMP_EINVAL, "instance %d outside [0, %d)", g, b->n);
+    const stamp_instance_desc& d = b->inst[g];
+    if (d.N > stamp::kMaxScreenN || n_candidates < d.N || n_candidates > stamp::surrogate_max_rows(s))
+        return bfail(STAMP_EINVAL, "need N <= %d and N <= n_candidates <= the surrogate's max_rows",
+                     stamp::kMaxScreenN);
+    // the instance's constants, as the batched rollouts see them
+    SimConst sc = b->phys;
+    sc.nb = d.n_blocks;
+    sc.H = d.H;
+    sc.M = 4 * sc.nb;
+    sc.P = sc.M + 2;
+    sc.D = b->D[g];
+    sc.S = 6 * sc.nb;
+    sc.n_ckpt = sc.H * sc.T / sc.C;
+    for (int k = 0; k < stamp::kMaxBlocks; ++k)
+        for (int j = 0; j < 3; ++j) {
+            sc.init[k][j] = k < d.n_blocks ? d.init[3 * k + j] : 0.f;
+            sc.goal[k][j] = k < d.n_blocks ? d.goal[3 * k + j] : 0.f;
+        }
+    B_CUDA(cudaStreamSynchronize(b->st));
+    const cudaStream_t ss = stamp::surrogate_stream(s);
+    float* cand = stamp::surrogate_candidates(s);
+    B_CUDA(stamp::launch_init_theta(cand, n_candidates, sc.D, d.seed, ss));
+    B_TRY(stamp::surrogate_screen(s, sc, cand, n_candidates, d.N, b->theta + b->elem0[g], nullptr));
+    B_CUDA(cudaStreamSynchronize(ss));
+    b->screened[g] = 1;
     return STAMP_OK;
 }
 

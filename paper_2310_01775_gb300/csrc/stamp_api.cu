@@ -484,13 +484,14 @@ bool lanes_supported(int nb, int lanes) {
     return false;
 }
 
-// Lanes per particle, from sweeps on GB300 (one block: 4/4; three blocks:
-// forward 32, adjoint 16).
+// Lanes per particle, from sweeps on GB300 (one block: 4/4; three blocks at
+// 2048 particles: forward 8 (0.76 ms against 0.82 at 16 and 0.90 at 32),
+// reverse sweep 16 (1.41 ms with the segment replay, 1.44 at 8, 2.11 at 32)).
 int default_lanes(int nb, int N, bool adjoint) {
     (void)N;
     if (nb == 1) return 4;
     if (nb == 2) return 8;
-    return adjoint ? 16 : 32;
+    return adjoint ? 16 : 8;
 }
 
 cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st) {

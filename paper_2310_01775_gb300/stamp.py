@@ -105,6 +105,7 @@ _sigs = {
     "stamp_inject_wait_timeout": [_vp],
     "stamp_set_particle_offset": [_vp, _i],
     "stamp_svgd_step_rows": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _f, _i, _vp, _vp],
+    "stamp_batch_screen": [_vp, _vp, _i, _i],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -578,6 +579,12 @@ class Batch:
                                         ctypes.byref(secs)))
         return {"iterations": it, "best_cost": best, "seconds_to_target": tts,
                 "top3": top3.reshape(self.n, 3), "units": units.value, "seconds": secs.value}
+
+    def screen(self, surrogate, instance, n_candidates):
+        """Start the instance's next solve from the N of n_candidates draws
+        with the lowest surrogate cost (stamp_batch_screen)."""
+        _check(_lib.stamp_batch_screen(self.handle, surrogate.handle, int(instance),
+                                       int(n_candidates)))
 
     def read_theta(self, instance, out):
         _check(_lib.stamp_batch_read_theta(self.handle, instance, _f32(out, "theta_out")))

@@ -205,3 +205,40 @@ def test_batched_plan_sets_match_the_oracle():
         plans = {tuple(int(x) for x in O.plan_codes(th[i:i + 1], P)[0]) for i in res["top3"][seed] if i >= 0}
         assert plans == {tuple(p) for p in gold[str(seed)]["f64"]["topk_plans"]}, seed
     b.close()
+
+
+def test_batch_screen_starts_from_the_surrogates_selection():
+    """stamp_batch_screen: the instance's next solve starts from the N of
+    n_candidates draws that stamp_surrogate_screen keeps for the same scene
+    and the same candidates (the solve's own U(-1,1) draws, which equal the
+    oracle's generator); unscreened instances start from their first N draws."""
+    from oracle import stamp_oracle as O
+    S = _S()
+    T = 50
+    stream = torch.cuda.current_stream().cuda_stream
+    insts = _instances(T)
+    b = _batch(insts, T)
+    sur = S.Surrogate(dict(W.PHYSICS, n_blocks=3, H=3, T=T, ckpt_every=25), 8192, 256, stream)
+    sur.init_params(5)
+    g, factor = 2, 16                         # instance 2: 3 blocks, H = 2, N = 100
+    d = insts[g]
+    n_cand = factor * d["N"]
+    b.screen(sur, g, n_cand)
+    b.solve(0, 1e-2)
+    D = d["H"] * (4 * d["n_blocks"] + 2)
+    got = torch.empty(d["N"], D, device="cuda")
+    b.read_theta(g, got)
+    P = dict(W.PHYSICS, n_blocks=3, H=d["H"], T=T, ckpt_every=25)
+    prob = S.Problem(P, d["init"], d["goal"], d["N"], stream)
+    cand = torch.tensor(O.init_theta(d["seed"], n_cand, D), dtype=torch.float32, device="cuda")
+    want = torch.empty(d["N"], D, device="cuda")
+    sur.screen(prob, cand, n_cand, d["N"], want)
+    sur.sync()
+    assert torch.equal(got, want)
+    other = torch.empty(insts[0]["N"], insts[0]["H"] * 6, device="cuda")
+    b.read_theta(0, other)
+    first = O.init_theta(insts[0]["seed"], insts[0]["N"], insts[0]["H"] * 6).astype(np.float32)
+    assert np.array_equal(other.cpu().numpy(), first)
+    prob.close()
+    sur.close()
+    b.close()
