@@ -37,10 +37,11 @@ UNIT = "particle-substeps/s"
 FLOPS_PER_UNIT = {1: (447.2, 863.2), 2: (2544.4, 5005.0), 3: (6293.5, 12860.9),
                   4: (11694.7, 24711.2)}
 FP32_LANES = 128                    # FP32 lanes per SM; 1 FMA = 2 FLOP
-# DRAM bytes (read + write) per launch of a rollout kernel, from one ncu
+# DRAM bytes (read + write) per launch of a rollout kernel (for the reverse
+# sweep: its replay and sweep launches together), from one cold-cache ncu
 # capture of the workload, valid while the kernel sources are unchanged
 # (sha256 prefix over the rollout sources at capture time).
-TRAFFIC = {}
+TRAFFIC = {("pusher3_h6", "rollout_adj"): ("5b9899d33b114c7b", 120.69e6)}   # replay + sweep
 ROLLOUT_SOURCES = ("rollout.cuh", "adjoint_time.cu")
 
 
@@ -238,7 +239,8 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
     done = np.where(stopped, r["seconds_to_target"], r["seconds"])
     b.close()
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
-    screened = batched_screened(insts, cfg, stream, iters, target, check_every, stopped) if screen else None
+    screened = (batched_screened(insts, cfg, stream, iters, target, check_every, r["seconds_to_target"])
+                if screen else None)
     return {"instances": n, "particles": int(sum(d["N"] for d in insts)),
             "units_per_iteration_all_active": int(sum(d["N"] * d["H"] * 100 for d in insts)),
             "value": r["units"] / r["seconds"], "unit": UNIT, "seconds": r["seconds"],
@@ -255,7 +257,7 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
             "surrogate_screened": screened}
 
 
-def batched_screened(insts, cfg, stream, iters, target, check_every, plain_stopped, factor=64):
+def batched_screened(insts, cfg, stream, iters, target, check_every, plain_tts, factor=64):
     """The same batch with surrogate screening: one surrogate per block count
     of 1-3 (trained on 2^20 simulator transitions of T=100 pushes; horizon up
     to 8), each instance of 1-3 blocks starting from the N of 64 N draws of
@@ -287,11 +289,16 @@ def batched_screened(insts, cfg, stream, iters, target, check_every, plain_stopp
     stopped = r["seconds_to_target"] >= 0
     tts = np.sort(r["seconds_to_target"][stopped] + screen_s)
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
-    both = stopped & plain_stopped
+    both = stopped & (plain_tts >= 0)
+    faster = int(np.sum(r["seconds_to_target"][both] + screen_s < plain_tts[both]))
     return {"reached": int(stopped.sum()), "reached_by_block_count": {
                 str(nb): f"{int(sum(stopped[g] for g, d in enumerate(insts) if d['n_blocks'] == nb))}"
                          f"/{sum(1 for d in insts if d['n_blocks'] == nb)}" for nb in range(1, 5)},
             "reached_by_both_arms": int(both.sum()),
+            "faster_than_plain_on_both_reached": faster,
+            "time_to_solution_both_reached_s": {
+                "screened_p50": pct(r["seconds_to_target"][both] + screen_s, 50),
+                "plain_p50": pct(plain_tts[both], 50)},
             "seconds": r["seconds"], "screening_seconds": round(screen_s, 3),
             "surrogate_training_seconds": round(train_s, 3),
             "time_to_solution_s": {"p50": pct(tts, 50), "p99": pct(tts, 99),

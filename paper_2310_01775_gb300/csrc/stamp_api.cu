@@ -484,14 +484,18 @@ bool lanes_supported(int nb, int lanes) {
     return false;
 }
 
-// Lanes per particle, from sweeps on GB300 (one block: 4/4; three blocks at
-// 2048 particles: forward 8 (0.76 ms against 0.82 at 16 and 0.90 at 32),
-// reverse sweep 16 (1.41 ms with the segment replay, 1.44 at 8, 2.11 at 32)).
+// Lanes per particle, from sweeps on GB300 at 2048 particles (H = 6, C = 25,
+// segment replay): one block 4/4; two blocks forward 8 (0.28 ms; 0.38 at 4,
+// 0.40 at 16), sweep 8 (0.50 ms; 0.60 at 16); three blocks forward 8
+// (0.76 ms; 0.82 at 16, 0.90 at 32), sweep 16 (1.41 ms; 1.44 at 8, 2.11 at
+// 32); four blocks forward 16 (1.28 ms; 1.39 at 8, 1.46 at 32), sweep 16
+// (2.37 ms; 3.09 at 8, 2.82 at 32).
 int default_lanes(int nb, int N, bool adjoint) {
     (void)N;
     if (nb == 1) return 4;
     if (nb == 2) return 8;
-    return adjoint ? 16 : 8;
+    if (nb == 3) return adjoint ? 16 : 8;
+    return 16;
 }
 
 cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lanes, cudaStream_t st) {
