@@ -246,6 +246,7 @@ __device__ __forceinline__ void disk_box(const SimConst& sc, float px, float py,
                                          float& tq) {
     fx = fy = tq = 0.f;
     const float dx = px - bx, dy = py - by;
+    if (dx * dx + dy * dy > sc.disk_reach2) return;   // out of reach: no contact
     const float lx = cph * dx + sph * dy, ly = -sph * dx + cph * dy;
     const float qx = fabsf(lx) - sc.hs, qy = fabsf(ly) - sc.hs;
     const float sx = lx >= 0.f ? 1.f : -1.f, sy = ly >= 0.f ? 1.f : -1.f;
@@ -280,6 +281,7 @@ __device__ __forceinline__ void corner_box(const SimConst& sc, float kx, float k
                                            float vx, float vy, float om, float& fx, float& fy) {
     fx = fy = 0.f;
     const float dx = kx - bx, dy = ky - by;
+    if (dx * dx + dy * dy > sc.corner_reach2) return;   // out of reach: no contact
     const float lx = cph * dx + sph * dy, ly = -sph * dx + cph * dy;
     const float qx = fabsf(lx) - sc.hs, qy = fabsf(ly) - sc.hs;
     if (!(qx < 0.f && qy < 0.f)) return;
@@ -549,6 +551,7 @@ __device__ __forceinline__ DiskGrad disk_box_vjp(const SimConst& sc, float px, f
                                                  float gT) {
     DiskGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float dx = px - bx, dy = py - by;
+    if (dx * dx + dy * dy > sc.disk_reach2) return g;   // out of reach: no contact
     const float lx = cph * dx + sph * dy, ly = -sph * dx + cph * dy;
     const float qx = fabsf(lx) - sc.hs, qy = fabsf(ly) - sc.hs;
     const float sx = lx >= 0.f ? 1.f : -1.f, sy = ly >= 0.f ? 1.f : -1.f;
@@ -649,6 +652,7 @@ __device__ __forceinline__ CornerGrad corner_vjp(const SimConst& sc, float xo, f
     const float kx = xo + rlx, ky = yo + rly;
     const float kvx = vxo - omo * rly, kvy = vyo + omo * rlx;
     const float dx = kx - xb, dy = ky - yb;
+    if (dx * dx + dy * dy > sc.corner_reach2) return g;   // out of reach: no contact
     const float lx = cb * dx + sb * dy, ly = -sb * dx + cb * dy;
     const float qx = fabsf(lx) - sc.hs, qy = fabsf(ly) - sc.hs;
     if (!(qx < 0.f && qy < 0.f)) return g;

@@ -590,6 +590,12 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
     sc.fric_lin = (float)((double)d->mu * d->mass * d->g);
     sc.fric_ang = (float)((double)d->mu * d->mass * d->g * r_eff);
     sc.eps_v2 = d->eps_v * d->eps_v; sc.eps_w2 = d->eps_w * d->eps_w; sc.eps_t2 = d->eps_t * d->eps_t;
+    {
+        const double circ = std::sqrt(2.0) * d->half_size;   // circumscribed radius of a block
+        const double dr = 1.001 * (circ + d->pusher_r), cr = 1.001 * circ;
+        sc.disk_reach2 = (float)(dr * dr);
+        sc.corner_reach2 = (float)(cr * cr);
+    }
     sc.inv_tau = (float)(1.0 / d->tau); sc.w_yaw = d->w_yaw; sc.w_push = d->w_push;
     sc.off_max = d->offset_max; sc.dist_max = d->dist_max;
     for (int b = 0; b < sc.nb; ++b)

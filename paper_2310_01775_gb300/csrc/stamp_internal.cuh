@@ -25,6 +25,10 @@ struct SimConst {
     float fric_lin;      // mu*m*g            (ground friction force scale)
     float fric_ang;      // mu*m*g*r_eff      (ground friction torque scale)
     float eps_v2, eps_w2, eps_t2;
+    // contact reach: a pusher centre farther than hs*sqrt(2) + r from a
+    // block centre, or a corner farther than hs*sqrt(2) from the other
+    // block's centre, cannot touch it (squared, 0.1% margin)
+    float disk_reach2, corner_reach2;
     float inv_tau, w_yaw, w_push, off_max, dist_max;
     float init[kMaxBlocks][3];
     float goal[kMaxBlocks][3];
