@@ -240,13 +240,15 @@ __device__ __forceinline__ void make_slots(const SimConst& sc, const Blocks<NB>&
 // ------------------------------- forces -------------------------------------
 // Force and torque on a square block (centre b, yaw via cph/sph, velocity v,
 // omega) from a kinematic disk pusher at p moving with vp (unweighted).
+// far_check: first test whether the pusher is out of reach (for items that
+// are rarely in contact; the pusher on its own object nearly always is).
 __device__ __forceinline__ void disk_box(const SimConst& sc, float px, float py, float vpx,
                                          float vpy, float bx, float by, float cph, float sph,
                                          float vx, float vy, float om, float& fx, float& fy,
-                                         float& tq) {
+                                         float& tq, bool far_check) {
     fx = fy = tq = 0.f;
     const float dx = px - bx, dy = py - by;
-    if (dx * dx + dy * dy > sc.disk_reach2) return;   // out of reach: no contact
+    if (far_check && dx * dx + dy * dy > sc.disk_reach2) return;   // out of reach: no contact
     const float lx = cph * dx + sph * dy, ly = -sph * dx + cph * dy;
     const float qx = fabsf(lx) - sc.hs, qy = fabsf(ly) - sc.hs;
     const float sx = lx >= 0.f ? 1.f : -1.f, sy = ly >= 0.f ? 1.f : -1.f;
@@ -313,9 +315,11 @@ __device__ __forceinline__ void substep_forces(const SimConst& sc, const Blocks<
         if (sl.c[q] < 0) continue;
         const int b = sl.b[q];
         float fx, fy, tq;
+        // slots past the first M items hold only pushers on other objects
         disk_box(sc, sl.p0x[q] + j1 * sl.dx[q], sl.p0y[q] + j1 * sl.dy[q], sl.dx[q] * sc.inv_dt,
                  sl.dy[q] * sc.inv_dt, pick(s.x, b), pick(s.y, b), pick(cs, b), pick(sn, b),
-                 pick(s.vx, b), pick(s.vy, b), pick(s.om, b), fx, fy, tq);
+                 pick(s.vx, b), pick(s.vy, b), pick(s.om, b), fx, fy, tq,
+                 q * L >= Dims<NB>::M);
         const float w = sl.w[q];
         add_at(Fx, b, w * fx);
         add_at(Fy, b, w * fy);
@@ -373,6 +377,24 @@ template <int NB>
 __device__ __forceinline__ void trig(const Blocks<NB>& s, float (&cs)[NB], float (&sn)[NB]) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) yaw_sincos(s.ph[b], &sn[b], &cs[b]);
+}
+// (cos, sin) of the blocks' yaws as NB float2; a team stores them split over
+// its lanes like the state.
+template <int NB, int L>
+__device__ __forceinline__ void store_trig(float2* dst, const float (&cs)[NB], const float (&sn)[NB],
+                                           int lane, bool on) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+        if (on && (b % L) == lane) dst[b] = make_float2(cs[b], sn[b]);
+}
+template <int NB>
+__device__ __forceinline__ void load_trig(const float2* src, float (&cs)[NB], float (&sn)[NB]) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const float2 v = src[b];
+        cs[b] = v.x;
+        sn[b] = v.y;
+    }
 }
 
 // State chunk q (of S/2 float2 chunks): block q/3, fields (x,y), (ph,vx), (vy,om).
@@ -548,10 +570,10 @@ __device__ __forceinline__ DiskGrad disk_box_vjp(const SimConst& sc, float px, f
                                                  float vpx, float vpy, float bx, float by,
                                                  float cph, float sph, float vx, float vy,
                                                  float om, float w, float gFx, float gFy,
-                                                 float gT) {
+                                                 float gT, bool far_check) {
     DiskGrad g = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float dx = px - bx, dy = py - by;
-    if (dx * dx + dy * dy > sc.disk_reach2) return g;   // out of reach: no contact
+    if (far_check && dx * dx + dy * dy > sc.disk_reach2) return g;   // out of reach: no contact
     const float lx = cph * dx + sph * dy, ly = -sph * dx + cph * dy;
     const float qx = fabsf(lx) - sc.hs, qy = fabsf(ly) - sc.hs;
     const float sx = lx >= 0.f ? 1.f : -1.f, sy = ly >= 0.f ? 1.f : -1.f;
@@ -764,7 +786,7 @@ __device__ __forceinline__ void substep_vjp(const SimConst& sc, const Blocks<NB>
             sc, sl.p0x[q] + j1 * sl.dx[q], sl.p0y[q] + j1 * sl.dy[q], sl.dx[q] * sc.inv_dt,
             sl.dy[q] * sc.inv_dt, pick(s.x, b), pick(s.y, b), pick(cs, b), pick(sn, b),
             pick(s.vx, b), pick(s.vy, b), pick(s.om, b), sl.w[q], pick(aFx, b), pick(aFy, b),
-            pick(aT, b));
+            pick(aT, b), q * L >= Dims<NB>::M);
         acc.p0x[q] += g.px;
         acc.p0y[q] += g.py;
         acc.dx[q] += j1 * g.px + g.vpx * sc.inv_dt;
@@ -851,15 +873,27 @@ __device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& 
 
         Blocks<NB> nxt;
         load_state(tape_i + (size_t)(k * segs + segs - 1) * ck2, nxt);
+        // with a replayed tape, the yaws' (cos, sin) come with the states
+        const bool have_trig = sc.C == 1 && a.trig != nullptr;
+        const size_t ckt = (size_t)a.N * NB;                         // float2 per trig row
+        const float2* trig_i = have_trig ? a.trig + (size_t)i * NB : nullptr;
+        float ncs[NB], nsn[NB];
+        if (have_trig) load_trig<NB>(trig_i + (size_t)(k * segs + segs - 1) * ckt, ncs, nsn);
         for (int sgi = segs - 1; sgi >= 0; --sgi) {
             s = nxt;
+            float cs[NB], sn[NB];
+            if (have_trig)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) { cs[b] = ncs[b]; sn[b] = nsn[b]; }
             // prefetch the previous checkpoint; its latency hides behind this
             // segment (nothing here touches it before the next iteration: warps
             // issue in order, so an early use would stall on the load)
-            if (sgi > 0) load_state(tape_i + (size_t)(k * segs + sgi - 1) * ck2, nxt);
+            if (sgi > 0) {
+                load_state(tape_i + (size_t)(k * segs + sgi - 1) * ck2, nxt);
+                if (have_trig) load_trig<NB>(trig_i + (size_t)(k * segs + sgi - 1) * ckt, ncs, nsn);
+            }
             if (sc.C == 1) {   // every state is on the tape: nothing to recompute
-                float cs[NB], sn[NB];
-                trig(s, cs, sn);
+                if (!have_trig) trig(s, cs, sn);
                 substep_vjp<NB, L>(sc, s, cs, sn, sl, acc, cn, (float)(sgi + 1), adj);
                 continue;
             }
@@ -1019,11 +1053,14 @@ __global__ void __launch_bounds__(128) replay_kernel(const SimConst sc, const Ro
     Corners<NB, L> cn;
     make_corners(cn, lane);
     const int t0 = k * sc.T + sg * sc.C;   // the segment's first substep
+    float2* trig_i = a.trig ? a.trig + (size_t)i * NB : nullptr;
+    const size_t ckt = (size_t)a.N * NB;
     for (int jj = 0; jj < sc.C; ++jj) {
         store_state<NB, L>(full_i + (size_t)(t0 + jj) * ck2, s, lane, on);
-        if (jj + 1 == sc.C) break;          // the state after it is the next checkpoint
         float cs[NB], sn[NB];
         trig(s, cs, sn);
+        if (trig_i) store_trig<NB, L>(trig_i + (size_t)(t0 + jj) * ckt, cs, sn, lane, on);
+        if (jj + 1 == sc.C) break;          // the state after it is the next checkpoint
         float Fx[NB], Fy[NB], Tq[NB];
         substep_forces<NB, L>(sc, s, cs, sn, sl, cn, (float)(sg * sc.C + jj + 1), Fx, Fy, Tq);
         integrate(sc, s, Fx, Fy, Tq);

@@ -79,6 +79,7 @@ struct stamp_problem {
     // segment replay (checkpoint interval > 1): the per-substep states of the
     // last forward, rebuilt in parallel, then swept at interval 1
     float* full = nullptr;
+    float2* full_trig = nullptr;   // the replayed states' yaw (cos, sin)
     bool replay_ok = false;
     // the bandwidth (pairwise distances + median) depends on theta only: the
     // solves run it on a second stream beside the rollouts
@@ -225,13 +226,15 @@ stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
     const int lanes = lanes_for(p, N, true);
     if (kind == STAMP_ADJ_REPLAY)
         return timed(p, STAMP_K_ROLLOUT_ADJ, [&] {
-            cudaError_t e = stamp::launch_replay(p->sc, a, stamp::replay_lanes(p->sc.nb), p->full,
+            stamp::RolloutArgs ar = a;
+            ar.trig = p->full_trig;
+            cudaError_t e = stamp::launch_replay(p->sc, ar, stamp::replay_lanes(p->sc.nb), p->full,
                                                  p->stream);
             if (e != cudaSuccess) return e;
             SimConst sc1 = p->sc;          // the rebuilt tape has interval 1
             sc1.C = 1;
             sc1.n_ckpt = sc1.H * sc1.T;
-            stamp::RolloutArgs a1 = a;
+            stamp::RolloutArgs a1 = ar;
             a1.tape = p->full;
             return stamp::launch_rollout_adj(sc1, a1, lanes, p->stream);
         });
@@ -487,14 +490,13 @@ bool lanes_supported(int nb, int lanes) {
 // Lanes per particle, from sweeps on GB300 at 2048 particles (H = 6, C = 25,
 // segment replay): one block 4/4; two blocks forward 8 (0.28 ms; 0.38 at 4,
 // 0.40 at 16), sweep 8 (0.50 ms; 0.60 at 16); three blocks forward 8
-// (0.76 ms; 0.82 at 16, 0.90 at 32), sweep 16 (1.41 ms; 1.44 at 8, 2.11 at
+// (0.75 ms; 0.82 at 16, 0.90 at 32), sweep 8 (1.28 ms; 1.38 at 16, 2.11 at
 // 32); four blocks forward 16 (1.28 ms; 1.39 at 8, 1.46 at 32), sweep 16
 // (2.37 ms; 3.09 at 8, 2.82 at 32).
 int default_lanes(int nb, int N, bool adjoint) {
     (void)N;
     if (nb == 1) return 4;
-    if (nb == 2) return 8;
-    if (nb == 3) return adjoint ? 16 : 8;
+    if (nb == 2 || nb == 3) return 8;
     return 16;
 }
 
@@ -643,6 +645,7 @@ stamp_status stamp_problem_create(const stamp_problem_desc* d, const float* init
         {(void**)&p->pit_rel, pit ? stamp::adjoint_time_rel_floats(max_particles, sc.H) * sizeof(float) : 0},
         {(void**)&p->pit_coef, pit ? pit_coef_bytes : 0},
         {(void**)&p->full, replay ? full_bytes : 0},
+        {(void**)&p->full_trig, replay ? (size_t)sc.H * sc.T * n * sc.nb * sizeof(float2) : 0},
     };
     p->pit_ok = pit;
     p->replay_ok = replay;

@@ -48,6 +48,9 @@ struct RolloutArgs {
     unsigned long long* dropped;   // count of particles whose reverse sweep overflowed
     const float* init_states;      // N x n_blocks x 3 initial poses (at rest), or NULL: the scene's
     int particle0;          // global index of row 0 (Gumbel draws of a shard of a larger set)
+    // per-substep (cos, sin) of every block's yaw, [H*T][N][NB] float2, or
+    // NULL: written by the segment replay, read by the sweep that follows it
+    float2* trig;
 };
 
 // One problem instance of a batch, as the batched rollout kernels see it.
