@@ -240,6 +240,13 @@ __device__ __forceinline__ void make_slots(const SimConst& sc, const Blocks<NB>&
 // ------------------------------- forces -------------------------------------
 // Force and torque on a square block (centre b, yaw via cph/sph, velocity v,
 // omega) from a kinematic disk pusher at p moving with vp (unweighted).
+// A pusher centre (corner) at offset (dx, dy) from a block centre farther
+// than the block's reach cannot touch it: the contact tests below return no
+// contact there, so callers may skip them.
+__device__ __forceinline__ bool out_of_reach(float dx, float dy, float reach2) {
+    return dx * dx + dy * dy > reach2;
+}
+
 // far_check: first test whether the pusher is out of reach (for items that
 // are rarely in contact; the pusher on its own object nearly always is).
 __device__ __forceinline__ void disk_box(const SimConst& sc, float px, float py, float vpx,
@@ -314,12 +321,15 @@ __device__ __forceinline__ void substep_forces(const SimConst& sc, const Blocks<
     for (int q = 0; q < Slots<NB, L>::SP; ++q) {
         if (sl.c[q] < 0) continue;
         const int b = sl.b[q];
+        const float px = sl.p0x[q] + j1 * sl.dx[q], py = sl.p0y[q] + j1 * sl.dy[q];
+        const float bx = pick(s.x, b), by = pick(s.y, b);
+        // slots past the first M items hold only pushers on other objects:
+        // one out of reach contributes nothing (skipped whole, by every lane
+        // of the warp when none has such an item in reach)
+        if (q * L >= Dims<NB>::M && out_of_reach(px - bx, py - by, sc.disk_reach2)) continue;
         float fx, fy, tq;
-        // slots past the first M items hold only pushers on other objects
-        disk_box(sc, sl.p0x[q] + j1 * sl.dx[q], sl.p0y[q] + j1 * sl.dy[q], sl.dx[q] * sc.inv_dt,
-                 sl.dy[q] * sc.inv_dt, pick(s.x, b), pick(s.y, b), pick(cs, b), pick(sn, b),
-                 pick(s.vx, b), pick(s.vy, b), pick(s.om, b), fx, fy, tq,
-                 q * L >= Dims<NB>::M);
+        disk_box(sc, px, py, sl.dx[q] * sc.inv_dt, sl.dy[q] * sc.inv_dt, bx, by, pick(cs, b),
+                 pick(sn, b), pick(s.vx, b), pick(s.vy, b), pick(s.om, b), fx, fy, tq, false);
         const float w = sl.w[q];
         add_at(Fx, b, w * fx);
         add_at(Fy, b, w * fy);
@@ -334,9 +344,10 @@ __device__ __forceinline__ void substep_forces(const SimConst& sc, const Blocks<
             const float clx = cn.ex[q] * sc.hs, cly = cn.ey[q] * sc.hs;
             const float rlx = co * clx - so * cly, rly = so * clx + co * cly;
             const float kx = pick(s.x, o) + rlx, ky = pick(s.y, o) + rly;
+            const float bx = pick(s.x, t), by = pick(s.y, t);
+            if (out_of_reach(kx - bx, ky - by, sc.corner_reach2)) continue;
             const float omo = pick(s.om, o);
             const float kvx = pick(s.vx, o) - omo * rly, kvy = pick(s.vy, o) + omo * rlx;
-            const float bx = pick(s.x, t), by = pick(s.y, t);
             float fx, fy;
             corner_box(sc, kx, ky, kvx, kvy, bx, by, pick(cs, t), pick(sn, t), pick(s.vx, t),
                        pick(s.vy, t), pick(s.om, t), fx, fy);
@@ -782,11 +793,15 @@ __device__ __forceinline__ void substep_vjp(const SimConst& sc, const Blocks<NB>
     for (int q = 0; q < Slots<NB, L>::SP; ++q) {
         if (sl.c[q] < 0) continue;
         const int b = sl.b[q];
+        const float px = sl.p0x[q] + j1 * sl.dx[q], py = sl.p0y[q] + j1 * sl.dy[q];
+        const float bx = pick(s.x, b), by = pick(s.y, b);
+        // as in substep_forces: an out-of-reach pusher on another object has
+        // a zero derivative
+        if (q * L >= Dims<NB>::M && out_of_reach(px - bx, py - by, sc.disk_reach2)) continue;
         const DiskGrad g = disk_box_vjp(
-            sc, sl.p0x[q] + j1 * sl.dx[q], sl.p0y[q] + j1 * sl.dy[q], sl.dx[q] * sc.inv_dt,
-            sl.dy[q] * sc.inv_dt, pick(s.x, b), pick(s.y, b), pick(cs, b), pick(sn, b),
-            pick(s.vx, b), pick(s.vy, b), pick(s.om, b), sl.w[q], pick(aFx, b), pick(aFy, b),
-            pick(aT, b), q * L >= Dims<NB>::M);
+            sc, px, py, sl.dx[q] * sc.inv_dt, sl.dy[q] * sc.inv_dt, bx, by, pick(cs, b),
+            pick(sn, b), pick(s.vx, b), pick(s.vy, b), pick(s.om, b), sl.w[q], pick(aFx, b),
+            pick(aFy, b), pick(aT, b), false);
         acc.p0x[q] += g.px;
         acc.p0y[q] += g.py;
         acc.dx[q] += j1 * g.px + g.vpx * sc.inv_dt;
@@ -804,6 +819,13 @@ __device__ __forceinline__ void substep_vjp(const SimConst& sc, const Blocks<NB>
         for (int q = 0; q < Corners<NB, L>::SC; ++q) {
             if (!cn.on[q]) continue;
             const int o = cn.own[q], t = cn.oth[q];
+            {   // a corner out of the other box's reach has a zero derivative
+                const float co = pick(cs, o), so = pick(sn, o);
+                const float clx = cn.ex[q] * sc.hs, cly = cn.ey[q] * sc.hs;
+                const float kx = pick(s.x, o) + co * clx - so * cly;
+                const float ky = pick(s.y, o) + so * clx + co * cly;
+                if (out_of_reach(kx - pick(s.x, t), ky - pick(s.y, t), sc.corner_reach2)) continue;
+            }
             const CornerGrad g = corner_vjp(
                 sc, pick(s.x, o), pick(s.y, o), pick(cs, o), pick(sn, o), pick(s.vx, o),
                 pick(s.vy, o), pick(s.om, o), pick(s.x, t), pick(s.y, t), pick(cs, t), pick(sn, t),
