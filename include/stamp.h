@@ -505,7 +505,9 @@ stamp_status stamp_solve_info(stamp_problem* prob, int* iterations_run, float* b
  * checks are captured once in a CUDA graph and replayed.  Each instance
  * computes what stamp_solve computes for it alone with the same lanes,
  * checkpoint interval and the sequential reverse sweep
- * (STAMP_ADJ_SEQUENTIAL; its particles start from the same draws). */
+ * (STAMP_ADJ_SEQUENTIAL; its particles start from the same draws), with
+ * the same kernel bodies compiled into separate kernels: results agree up
+ * to the rounding of multiply-adds the compiler fuses differently. */
 typedef struct stamp_batch stamp_batch;
 typedef struct {
     int n_blocks, H, N;            /* 1..4 blocks, 1..16 actions, 1..8192 particles */

@@ -8,9 +8,11 @@
 // a counter bump; a run of iterations between early-stop checks is captured
 // once in a CUDA graph and replayed.  The iteration number and Adam's step
 // live on the device, so the replayed launches see them advance.  Every
-// instance computes exactly what stamp_solve computes for it alone with the
-// same lanes, checkpoint interval and the sequential reverse sweep (same
-// kernels, same Stein-sum split, same bias-correction constants).
+// instance computes what stamp_solve computes for it alone with the same
+// lanes, checkpoint interval and the sequential reverse sweep (same kernel
+// bodies, same Stein-sum split, same bias-correction constants), up to the
+// rounding of multiply-adds the compiler fuses differently in the two
+// kernels.
 #include <algorithm>
 #include <chrono>
 #include <cstdarg>
