@@ -288,6 +288,10 @@ stamp_status stamp_inject_wait_timeout(stamp_problem* prob);
 
 /* Lanes per particle used by the rollout kernels (1,2,4,8,16,32; 0 = automatic). */
 stamp_status stamp_set_lanes(stamp_problem* prob, int fwd_lanes, int adj_lanes);
+/* Lanes per (particle, segment) team of the segment replay (STAMP_ADJ_REPLAY):
+ * one block 1, 2, 4; two blocks 2..16; three blocks 2..32; four blocks
+ * 4..32; 0 = automatic. */
+stamp_status stamp_set_replay_lanes(stamp_problem* prob, int lanes);
 
 /* Stein step without any device allocation.  The paper has no counterpart:
  * this serves callers that cannot call cudaMalloc -- code whose device memory
@@ -562,7 +566,8 @@ stamp_status stamp_batch_read_theta(stamp_batch* batch, int instance, float* the
  * the instance's next stamp_batch_solve from them instead of its first N
  * draws.  The surrogate must model the instance's block count and a horizon
  * >= its H; N <= 4096, N <= n_candidates <= the surrogate's max_rows.  Runs
- * on the surrogate's stream and waits for it. */
+ * on the surrogate's stream and waits for it.  stamp_batch_autotune in
+ * between keeps the screened particles; the solve consumes them. */
 stamp_status stamp_batch_screen(stamp_batch* batch, stamp_surrogate* surrogate, int instance,
                                 int n_candidates);
 

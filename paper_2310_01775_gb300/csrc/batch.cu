@@ -513,11 +513,11 @@ stamp_status stamp_batch_autotune(stamp_batch* b, int reps) {
     if (!b) return bfail(STAMP_EINVAL, "NULL batch");
     if (reps < 1) reps = 1;
     B_CUDA(cudaStreamSynchronize(b->user));
+    // the solve's initial particles (screened ones stay, for the next solve)
     for (int g = 0; g < b->n; ++g)
         if (!b->screened[g])
             B_CUDA(stamp::launch_init_theta(b->theta + b->elem0[g], b->inst[g].N, b->D[g],
                                             b->inst[g].seed, b->st));
-    b->screened.assign(b->n, 0);
     std::vector<int> ones(b->n, 1);
     B_CUDA(cudaMemcpyAsync(b->active, ones.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->st));
     B_CUDA(cudaMemsetAsync(b->iter, 0, sizeof(int), b->st));

@@ -527,16 +527,31 @@ mlp_dw_tc_kernel(const unsigned char* __restrict__ P, int KP, size_t p_stride,
     for (int t = t0; t < t1 && !failed; ++t) {
         const unsigned char* Pt = P + (size_t)t * p_stride;
         const unsigned char* Qt = Q + (size_t)t * q_stride;
-        // core matrix c: row group gs (8 rows) of unit group gu, transposed
-        for (int c = warp; c < nA + nB; c += kThreads / 32) {
-            const bool isA = c < nA;
-            const int cc = isA ? c : c - nA, gs = cc & 15, gu = cc >> 4;
-            const unsigned char* src = isA ? Pt + gs * (KP / 8) * 128 + (mb * 16 + gu) * 128
-                                           : Qt + gs * (NQ / 8) * 128 + gu * 128;
-            unsigned char* dst = (isA ? sm.A : sm.B) + gu * 2048 + gs * 128;
-            const int off = (lane >> 2) * 16 + (lane & 3) * 4;
-            *reinterpret_cast<unsigned*>(dst + off) =
-                transpose8x8(__ldg(reinterpret_cast<const unsigned*>(src + off)));
+        // core matrix c: row group gs (8 rows) of unit group gu, transposed;
+        // each warp first issues the loads of kBatch core matrices, so that
+        // many are in flight, then transposes and stores them
+        constexpr int kBatch = 8, kWarps = kThreads / 32;
+        const int off = (lane >> 2) * 16 + (lane & 3) * 4;
+        for (int c0 = warp; c0 < nA + nB; c0 += kBatch * kWarps) {
+            unsigned w[kBatch];
+            unsigned char* dst[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int c = c0 + u * kWarps;
+                dst[u] = nullptr;
+                if (c < nA + nB) {
+                    const bool isA = c < nA;
+                    const int cc = isA ? c : c - nA, gs = cc & 15, gu = cc >> 4;
+                    const unsigned char* src = isA ? Pt + gs * (KP / 8) * 128 + (mb * 16 + gu) * 128
+                                                   : Qt + gs * (NQ / 8) * 128 + gu * 128;
+                    dst[u] = (isA ? sm.A : sm.B) + gu * 2048 + gs * 128 + off;
+                    w[u] = __ldg(reinterpret_cast<const unsigned*>(src + off));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (c0 + u * kWarps < nA + nB)   // warp-uniform: movmatrix needs the whole warp
+                    *reinterpret_cast<unsigned*>(dst[u]) = transpose8x8(w[u]);
         }
         fence_async_shared();
         tc_fence_before();

@@ -26,6 +26,8 @@ cudaError_t launch_rollout_batch_nb3(const SimConst& sc, const BatchArgs& b, int
 cudaError_t launch_replay_nb3(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
                                 cudaStream_t st) {
     switch (lanes) {
+        case 2: return rollout::launch_replay<3, 2>(sc, a, full, st);
+        case 4: return rollout::launch_replay<3, 4>(sc, a, full, st);
         case 8: return rollout::launch_replay<3, 8>(sc, a, full, st);
         case 16: return rollout::launch_replay<3, 16>(sc, a, full, st);
         case 32: return rollout::launch_replay<3, 32>(sc, a, full, st);

@@ -26,6 +26,7 @@ cudaError_t launch_rollout_batch_nb4(const SimConst& sc, const BatchArgs& b, int
 cudaError_t launch_replay_nb4(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
                                 cudaStream_t st) {
     switch (lanes) {
+        case 4: return rollout::launch_replay<4, 4>(sc, a, full, st);
         case 8: return rollout::launch_replay<4, 8>(sc, a, full, st);
         case 16: return rollout::launch_replay<4, 16>(sc, a, full, st);
         case 32: return rollout::launch_replay<4, 32>(sc, a, full, st);

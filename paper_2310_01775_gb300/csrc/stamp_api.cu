@@ -70,7 +70,7 @@ struct stamp_problem {
     int last_n = 0, last_iter = 0, last_hard = 0, last_particle0 = 0;
     unsigned long long last_seed = 0;
     const float* last_theta = nullptr;
-    int fwd_lanes = 0, adj_lanes = 0;
+    int fwd_lanes = 0, adj_lanes = 0, replay_lanes = 0;
     // one-block reverse sweep as a linear recurrence in time (checkpoint
     // interval 1): its scratch exists when the problem qualifies
     int adj_mode = STAMP_ADJ_AUTO;
@@ -228,8 +228,8 @@ stamp_status adj(stamp_problem* p, const float* theta, int N, float* grad) {
         return timed(p, STAMP_K_ROLLOUT_ADJ, [&] {
             stamp::RolloutArgs ar = a;
             ar.trig = p->full_trig;
-            cudaError_t e = stamp::launch_replay(p->sc, ar, stamp::replay_lanes(p->sc.nb), p->full,
-                                                 p->stream);
+            const int rl = p->replay_lanes ? p->replay_lanes : stamp::replay_lanes(p->sc.nb);
+            cudaError_t e = stamp::launch_replay(p->sc, ar, rl, p->full, p->stream);
             if (e != cudaSuccess) return e;
             SimConst sc1 = p->sc;          // the rebuilt tape has interval 1
             sc1.C = 1;
@@ -512,7 +512,7 @@ cudaError_t launch_rollout_fwd(const SimConst& sc, const RolloutArgs& a, int lan
 
 // The fewest lanes each block count supports: the replay is throughput
 // bound, and fewer lanes integrate the state less redundantly.
-int replay_lanes(int nb) { return nb == 1 ? 1 : nb == 2 ? 2 : 8; }
+int replay_lanes(int nb) { return nb == 1 ? 1 : nb == 2 ? 2 : nb == 3 ? 4 : 8; }
 
 cudaError_t launch_replay(const SimConst& sc, const RolloutArgs& a, int lanes, float* full,
                           cudaStream_t st) {
@@ -703,6 +703,17 @@ stamp_status stamp_set_lanes(stamp_problem* p, int fwd_lanes, int adj_lanes) {
         return fail(STAMP_EINVAL, "unsupported lane count for n_blocks=%d", p->sc.nb);
     p->fwd_lanes = fwd_lanes;
     p->adj_lanes = adj_lanes;
+    return STAMP_OK;
+}
+
+stamp_status stamp_set_replay_lanes(stamp_problem* p, int lanes) {
+    if (!p) return fail(STAMP_EINVAL, "NULL problem");
+    // the replay's instantiations: one block 1-4, two 2-16, three 2-32, four 4-32 lanes
+    const int lo = p->sc.nb == 1 ? 1 : p->sc.nb == 4 ? 4 : 2, hi = p->sc.nb == 1 ? 4 : p->sc.nb == 2 ? 16 : 32;
+    const bool pow2 = lanes > 0 && (lanes & (lanes - 1)) == 0;
+    if (lanes != 0 && !(pow2 && lanes >= lo && lanes <= hi))
+        return fail(STAMP_EINVAL, "unsupported replay lane count %d for n_blocks=%d", lanes, p->sc.nb);
+    p->replay_lanes = lanes;
     return STAMP_OK;
 }
 

@@ -106,6 +106,7 @@ _sigs = {
     "stamp_set_particle_offset": [_vp, _i],
     "stamp_svgd_step_rows": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _f, _i, _vp, _vp],
     "stamp_batch_screen": [_vp, _vp, _i, _i],
+    "stamp_set_replay_lanes": [_vp, _i],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -339,6 +340,10 @@ class Problem:
 
     def set_lanes(self, fwd_lanes, adj_lanes):
         stamp_set_lanes(self.handle, fwd_lanes, adj_lanes)
+
+    def set_replay_lanes(self, lanes):
+        """Lanes per (particle, segment) team of the segment replay (0: automatic)."""
+        _check(_lib.stamp_set_replay_lanes(self.handle, int(lanes)))
 
     def set_particle_offset(self, particle0):
         """Later rollouts' row r is particle particle0 + r of a larger set."""

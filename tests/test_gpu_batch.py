@@ -220,7 +220,8 @@ def test_batch_screen_starts_from_the_surrogates_selection():
     """stamp_batch_screen: the instance's next solve starts from the N of
     n_candidates draws that stamp_surrogate_screen keeps for the same scene
     and the same candidates (the solve's own U(-1,1) draws, which equal the
-    oracle's generator); unscreened instances start from their first N draws."""
+    oracle's generator), also across an autotuning run in between;
+    unscreened instances start from their first N draws."""
     from oracle import stamp_oracle as O
     S = _S()
     T = 50
@@ -233,6 +234,7 @@ def test_batch_screen_starts_from_the_surrogates_selection():
     d = insts[g]
     n_cand = factor * d["N"]
     b.screen(sur, g, n_cand)
+    b.autotune(1)                             # keeps the screened particles
     b.solve(0, 1e-2)
     D = d["H"] * (4 * d["n_blocks"] + 2)
     got = torch.empty(d["N"], D, device="cuda")
