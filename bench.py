@@ -202,7 +202,8 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
                     screen=True):
     """256 seeded uneven instances (1-4 blocks, H 2-8, N log-uniform 64-1024,
     T=100; goals planted: the end poses of a hard rollout of a random plan)
-    solved together: autotuned launch configuration, graph-replayed
+    solved together: autotuned launch configuration and launch mode (per-class
+    launches or one persistent launch per iteration; both timed), graph-replayed
     iterations, per-instance early stop at the target (hard simulator check
     every 10 iterations), at most 500 iterations; then the same batch with
     surrogate screening (batched_screened)."""
@@ -226,6 +227,16 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
     b.autotune(2)
     tune_s = time.perf_counter() - t0
     cfg = {str(nb): dict(zip(("lanes", "cta", "ckpt_every"), b.get_config(nb))) for nb in range(1, 5)}
+    persistent, tune_ms_a, tune_ms_p = b.persistent()
+    # both launch modes over 20 graph-replayed iterations of every instance
+    # (no early-stop checks; the second of two solves, after the capture)
+    mode_ms = {}
+    for name, flag in (("per_class", False), ("persistent", True)):
+        b.set_persistent(flag)
+        for _ in range(2):
+            b.solve(20, 1e-2, 0.0, 0, True)
+        mode_ms[name] = b.results()["seconds"] / 20 * 1e3
+    b.set_persistent(persistent)
     b.solve(iters, 1e-2, target, check_every, True)
     r = b.results()
     stopped = r["seconds_to_target"] >= 0
@@ -239,12 +250,18 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
     done = np.where(stopped, r["seconds_to_target"], r["seconds"])
     b.close()
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
-    screened = (batched_screened(insts, cfg, stream, iters, target, check_every, r["seconds_to_target"])
-                if screen else None)
+    screened = (batched_screened(insts, cfg, persistent, stream, iters, target, check_every,
+                                 r["seconds_to_target"]) if screen else None)
     return {"instances": n, "particles": int(sum(d["N"] for d in insts)),
             "units_per_iteration_all_active": int(sum(d["N"] * d["H"] * 100 for d in insts)),
             "value": r["units"] / r["seconds"], "unit": UNIT, "seconds": r["seconds"],
             "autotune_seconds": round(tune_s, 3), "config_per_block_count": cfg,
+            "launch_mode": "persistent" if persistent else "per-class",
+            "ms_per_iteration_all_active": {
+                "per_class": mode_ms["per_class"], "persistent": mode_ms["persistent"],
+                "autotune_per_class": tune_ms_a, "autotune_persistent": tune_ms_p,
+                "over": "20 graph-replayed iterations of every instance, solve wall time incl. "
+                        "initialisation and final evaluation / 20"},
             "target_cost": target, "reached": int(stopped.sum()),
             "time_to_solution_s": {"p50": pct(tts, 50), "p99": pct(tts, 99),
                                    "over": "instances that reached the target"},
@@ -254,10 +271,43 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "over": "the whole solve (all kernels, checks included)",
                          "peak_source": peak_src},
-            "surrogate_screened": screened}
+            "surrogate_screened": screened,
+            "small_requests": small_requests(stream)}
 
 
-def batched_screened(insts, cfg, stream, iters, target, check_every, plain_tts, factor=64):
+def small_requests(stream, n=512, N=32, iters=40):
+    """Many small requests: n seeded instances of N particles each (1-4
+    blocks, H 2-4, T=100) -- the latency-bound end of serving.  Autotuned
+    launch configuration and mode; milliseconds per graph-replayed iteration
+    of every instance in both launch modes."""
+    from paper_2310_01775_gb300 import stamp as S
+    from paper_2310_01775_gb300 import workloads as W
+    rng = np.random.default_rng(np.random.SeedSequence([0, 0x5A11]))
+    insts = []
+    for g in range(n):
+        nb, H = int(rng.integers(1, 5)), int(rng.integers(2, 5))
+        init, goal = W.scene(dict(W.PHYSICS, n_blocks=nb, H=H, T=100), 30011 + g)
+        insts.append({"n_blocks": nb, "H": H, "N": N, "seed": 50021 + g, "init": init, "goal": goal})
+    b = S.Batch(dict(W.PHYSICS, T=100), insts, stream)
+    b.autotune(2)
+    persistent, _, _ = b.persistent()
+    ms = {}
+    for name, flag in (("per_class", False), ("persistent", True)):
+        b.set_persistent(flag)
+        for _ in range(2):
+            b.solve(iters, 1e-2, 0.0, 0, True)
+        ms[name] = b.results()["seconds"] / iters * 1e3
+    units = sum(d["N"] * d["H"] * 100 for d in insts)
+    b.close()
+    return {"instances": n, "particles_each": N, "launch_mode": "persistent" if persistent else "per-class",
+            "ms_per_iteration_all_active": ms,
+            "value": units / (min(ms.values()) / 1e3), "unit": UNIT,
+            "over": f"{iters} graph-replayed iterations, solve wall time incl. initialisation and "
+                    f"final evaluation / {iters}"}
+
+
+def batched_screened(insts, cfg, persistent, stream, iters, target, check_every, plain_tts,
+                     factor=64):
     """The same batch with surrogate screening: one surrogate per block count
     of 1-3 (trained on 2^20 simulator transitions of T=100 pushes; horizon up
     to 8), each instance of 1-3 blocks starting from the N of 64 N draws of
@@ -276,6 +326,7 @@ def batched_screened(insts, cfg, stream, iters, target, check_every, plain_tts, 
     b = S.Batch(dict(W.PHYSICS, T=100), insts, stream)
     for nb, c in cfg.items():
         b.set_config(int(nb), c["lanes"], c["cta"], c["ckpt_every"])
+    b.set_persistent(persistent)
     t0 = time.perf_counter()
     for g, d in enumerate(insts):
         if d["n_blocks"] in surs:

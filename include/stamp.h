@@ -502,16 +502,24 @@ stamp_status stamp_solve_info(stamp_problem* prob, int* iterations_run, float* b
  * Many planning problems solved together (Algorithm 1 on each), for serving
  * uneven requests on one GPU.  All instances share the physics (T, dt,
  * contact, friction, tau, cost weights) and differ in block count, horizon,
- * particle count, scene and seed.  Per Stein iteration the batch issues one
- * forward and one adjoint launch per block-count class, one launch each for
- * the pairwise distances, the two median digits, the Stein direction and
- * Adam over all instances, and a counter bump; iterations between early-stop
- * checks are captured once in a CUDA graph and replayed.  Each instance
- * computes what stamp_solve computes for it alone with the same lanes,
- * checkpoint interval and the sequential reverse sweep
- * (STAMP_ADJ_SEQUENTIAL; its particles start from the same draws), with
- * the same kernel bodies compiled into separate kernels: results agree up
- * to the rounding of multiply-adds the compiler fuses differently. */
+ * particle count, scene and seed.  A Stein iteration of the whole batch runs
+ * in one of two launch modes:
+ *   per-class: one forward and one adjoint launch per block-count class, one
+ *     launch each for the pairwise distances, the two median digits, the
+ *     Stein direction and Adam over all instances, and a counter bump;
+ *   persistent: ONE launch, a grid of the GPU's resident CTAs that take work
+ *     items from a device-wide queue -- every instance's rollouts (each
+ *     warp's forward followed at once by its adjoint; lanes 2/4/8/8 for
+ *     1/2/3/4 blocks), pairwise tiles, median passes, Stein blocks and Adam
+ *     chunks -- each item waiting (bounded, 1 s) only on earlier items of
+ *     its own instance.
+ * Either way, the iterations between early-stop checks are captured once in
+ * a CUDA graph and replayed.  Each instance computes what stamp_solve
+ * computes for it alone with the same lanes, checkpoint interval and the
+ * sequential reverse sweep (STAMP_ADJ_SEQUENTIAL; its particles start from
+ * the same draws), with the same kernel bodies compiled into other kernels:
+ * results agree up to the rounding of multiply-adds the compiler fuses
+ * differently.  Both modes are deterministic run to run. */
 typedef struct stamp_batch stamp_batch;
 typedef struct {
     int n_blocks, H, N;            /* 1..4 blocks, 1..16 actions, 1..8192 particles */
@@ -536,8 +544,24 @@ stamp_status stamp_batch_get_config(stamp_batch* batch, int n_blocks, int* lanes
                                     int* ckpt_every);
 /* Autotuner: per class, times `reps` forward + adjoint launches for each
  * supported lane count, CTA size 64/128 and checkpoint interval 1/5/25 on
- * the solve's initial particles, and keeps the fastest.  Waits. */
+ * the solve's initial particles, and keeps the fastest; then times `reps`
+ * whole iterations in each launch mode (the persistent mode with the tuned
+ * checkpoint intervals) and keeps the faster mode.  The particles are left
+ * as they were (screened ones included).  Waits. */
 stamp_status stamp_batch_autotune(stamp_batch* batch, int reps);
+/* Launch mode: on != 0 the persistent launch, 0 the per-class launches (the
+ * default until stamp_batch_autotune picks).  The get call also returns the
+ * autotuner's milliseconds per iteration in each mode (-1 before it ran);
+ * any pointer may be NULL. */
+stamp_status stamp_batch_set_persistent(stamp_batch* batch, int on);
+stamp_status stamp_batch_get_persistent(stamp_batch* batch, int* on, float* ms_per_class,
+                                        float* ms_persistent);
+/* Error-path test: in the next stamp_batch_solve only, the persistent
+ * launch's Stein items wait for one rollout warp more than exist, with a
+ * 2 ms limit.  The wait runs out, the launch drains its queue, and the solve
+ * returns STAMP_ETIMEOUT; the solve after it is clean.  No effect on the
+ * per-class mode. */
+stamp_status stamp_batch_inject_wait_timeout(stamp_batch* batch);
 /* Algorithm 1 (SVGD phase) on every instance for up to `iters` (<= 65536)
  * iterations at Adam rate lr.  check_every > 0: every check_every iterations
  * all running instances are rolled out hard without noise and an instance
@@ -559,6 +583,9 @@ stamp_status stamp_batch_results(stamp_batch* batch, int* iterations, float* bes
                                  double* seconds);
 /* Copy one instance's particles (N x D) to host or device memory. */
 stamp_status stamp_batch_read_theta(stamp_batch* batch, int instance, float* theta_out);
+/* Copy one instance's grad log rho (N x D) of the last Stein iteration the
+ * batch ran (in the last solve, or the autotuner's timing runs). */
+stamp_status stamp_batch_read_grad(stamp_batch* batch, int instance, float* grad_out);
 /* Surrogate screening for a batched instance (the surrogate-assisted solve's
  * first step, for serving): draw n_candidates particles theta ~ U(-1,1)^D
  * from the instance's seed (the draws stamp_solve_surrogate makes), keep the

@@ -13,8 +13,14 @@
 // bodies, same Stein-sum split, same bias-correction constants), up to the
 // rounding of multiply-adds the compiler fuses differently in the two
 // kernels.
+//
+// Or, in the persistent mode (batch_persist.cu), one launch per iteration
+// does all of it: a work queue over every instance's rollouts (forward and
+// adjoint fused per warp), pairwise tiles, median passes, Stein blocks and
+// Adam chunks.  The autotuner times both modes and keeps the faster.
 #include <algorithm>
 #include <chrono>
+#include <queue>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -57,6 +63,7 @@ stamp_status bfail(stamp_status s, const char* fmt, ...) {
 constexpr int kMaxInstances = 4096;
 constexpr int kMedCtasMax = 64;
 constexpr int kMaxIters = 1 << 16;   // Adam bias-correction table length
+constexpr unsigned long long kWaitNs = 1000000000ull;   // persistent dependency waits: 1 s
 
 __global__ void bump_kernel(int* iter, int* step) {
     ++*iter;
@@ -128,6 +135,20 @@ struct stamp_batch {
     int graph_iters = 0;
     float graph_lr = 0.f;
     bool graph_dirty = true;
+    // persistent iteration (one launch per iteration)
+    bool persist = false;
+    bool persist_dirty = true;       // class intervals changed: rebuild p_inst, grid
+    int persist_grid = 0;
+    size_t persist_smem = 0;
+    stamp::PersistArgs pa{};
+    SimConst cls_sc[stamp::kMaxBlocks]{};
+    BatchInst* p_inst = nullptr;
+    int4 *p_need = nullptr, *p_warps = nullptr, *p_phi = nullptr;
+    int2* p_adam = nullptr;
+    unsigned *p_ctr = nullptr, *p_dep = nullptr;
+    int extra_wait = 0;              // > 0 for the next solve: its Stein items' waits run out
+    unsigned long long wait_ns = kWaitNs;
+    float mode_ms[2] = {-1.f, -1.f};   // autotuner: ms per iteration, per-class and persistent
     // instances whose next solve starts from particles set by stamp_batch_screen
     std::vector<char> screened;
     // last solve
@@ -170,6 +191,32 @@ stamp_status build_class_tables(stamp_batch* b, Class& c) {
     c.sc.C = c.C;
     B_CUDA(cudaMemcpy(c.d_inst, h.data(), h.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
     b->graph_dirty = true;
+    b->persist_dirty = true;
+    return STAMP_OK;
+}
+
+// The persistent launch's per-instance table (each instance with its class's
+// checkpoint interval), the adjoint's segment memory per warp, the grid.
+// Synchronous: never while a graph is being captured.
+stamp_status ensure_persist(stamp_batch* b) {
+    if (!b->persist_dirty) return STAMP_OK;
+    std::vector<BatchInst> h(b->n);
+    int seg_warp = 0;
+    for (const Class& c : b->cls) {
+        std::vector<BatchInst> ci(c.members.size());
+        B_CUDA(cudaMemcpy(ci.data(), c.d_inst, ci.size() * sizeof(BatchInst), cudaMemcpyDeviceToHost));
+        for (size_t q = 0; q < c.members.size(); ++q) h[c.members[q]] = ci[q];
+        const int L = stamp::persist_lanes(c.nb);
+        if (c.C > 1) seg_warp = std::max(seg_warp, (32 / L) * (c.C * 3 * c.nb + 1));
+        b->cls_sc[c.nb - 1] = c.sc;
+    }
+    B_CUDA(cudaMemcpy(b->p_inst, h.data(), h.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
+    b->persist_smem = stamp::persist_smem(b->max_D, seg_warp);
+    if (b->persist_smem > 200 * 1024) return bfail(STAMP_EINVAL, "checkpoint segments too large for the persistent launch");
+    B_CUDA(stamp::persist_grid(b->persist_smem, &b->persist_grid));
+    b->pa.seg_warp = seg_warp;
+    b->persist_dirty = false;
+    b->graph_dirty = true;
     return STAMP_OK;
 }
 
@@ -196,6 +243,15 @@ stamp_status rollout_class(stamp_batch* b, const Class& c, bool adjoint, bool ha
 // the Stein direction waits for both (fork and join become graph edges when
 // captured).
 stamp_status iteration(stamp_batch* b, cudaStream_t st) {
+    if (b->persist) {
+        if (b->persist_dirty) return bfail(STAMP_EINVAL, "persistent tables out of date");
+        stamp::PersistArgs pa = b->pa;
+        pa.lr = b->lr;
+        pa.extra_wait = b->extra_wait;
+        pa.wait_ns = b->wait_ns;
+        B_CUDA(stamp::launch_persist(pa, b->cls_sc, b->persist_grid, b->persist_smem, st));
+        return STAMP_OK;
+    }
     B_CUDA(cudaEventRecord(b->ev_fork, st));
     B_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
     B_CUDA(cudaMemsetAsync(b->hist, 0, b->hist_bytes, b->side));
@@ -250,6 +306,106 @@ stamp_status hard_eval(stamp_batch* b, bool all) {
     for (const Class& c : b->cls) B_TRY(rollout_class(b, c, false, true, b->st));
     instance_min_kernel<<<b->n, 256, 0, b->st>>>(b->cost, b->cost0_dev, b->nvec, b->inst_min);
     B_CUDA(cudaGetLastError());
+    return STAMP_OK;
+}
+
+// Work queue of the persistent launch.  Rollout items go longest first: a
+// warp task's time is estimated as horizon x a per-block-count cost (per-warp
+// rollout + adjoint time per action, measured on GB300 with the per-class
+// kernels at their tuned lanes).  The Stein blocks and Adam chunks follow in
+// the order in which a list schedule of the rollout items over one CTA per
+// SM finishes the instances' rollouts.
+stamp_status build_persist_queue(stamp_batch* b, const std::vector<SvgdInst>& si) {
+    static const double kCost[stamp::kMaxBlocks] = {0.17, 0.39, 0.52, 1.09};
+    constexpr int W = stamp::kPersistWarps;
+    struct Task { double t; int g, first, nb; };
+    std::vector<Task> tasks;
+    std::vector<int4> need(b->n);
+    for (int g = 0; g < b->n; ++g) {
+        const stamp_instance_desc& d = b->inst[g];
+        const int tpw = 32 / stamp::persist_lanes(d.n_blocks);
+        const int warps = (d.N + tpw - 1) / tpw;
+        for (int w = 0; w < warps; ++w) tasks.push_back({d.H * kCost[d.n_blocks - 1], g, w * tpw, d.n_blocks});
+        const int rb = (d.N + stamp::kPersistRows - 1) / stamp::kPersistRows;
+        need[g] = make_int4(warps, si[g].nt * (si[g].nt + 1) / 2, si[g].med_ctas, si[g].shares * rb);
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [](const Task& x, const Task& y) { return x.t > y.t; });
+    const int n_roll = (int)((tasks.size() + W - 1) / W);
+    std::vector<int4> warps((size_t)n_roll * W, make_int4(-1, 0, 0, 0));
+    for (size_t q = 0; q < tasks.size(); ++q) warps[q] = make_int4(tasks[q].g, tasks[q].first, tasks[q].nb, 0);
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int w = 0; w < stamp::sm_count(); ++w) free_at.push(0.0);
+    std::vector<double> done(b->n, 0.0);
+    for (int it = 0; it < n_roll; ++it) {
+        double dur = 0.0;
+        for (int w = 0; w < W && (size_t)it * W + w < tasks.size(); ++w) dur = std::max(dur, tasks[(size_t)it * W + w].t);
+        const double t1 = free_at.top() + dur;
+        free_at.pop();
+        free_at.push(t1);
+        for (int w = 0; w < W && (size_t)it * W + w < tasks.size(); ++w) {
+            const int g = tasks[(size_t)it * W + w].g;
+            done[g] = std::max(done[g], t1);
+        }
+    }
+    std::vector<int> order(b->n);
+    for (int g = 0; g < b->n; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return done[x] < done[y]; });
+    std::vector<int4> phi;
+    std::vector<int2> adam;
+    for (int g : order) {
+        const int rb = (b->inst[g].N + stamp::kPersistRows - 1) / stamp::kPersistRows;
+        for (int sh = 0; sh < si[g].shares; ++sh)
+            for (int r0 = 0; r0 < rb; ++r0) phi.push_back(make_int4(g, r0, sh, 0));
+    }
+    for (int g : order) {
+        const long long ne = (long long)b->inst[g].N * b->D[g];
+        for (long long c = 0; c * stamp::kPersistAdamChunk < ne; ++c) adam.push_back(make_int2(g, (int)c));
+    }
+    B_CUDA(cudaMalloc(&b->p_warps, warps.size() * sizeof(int4)));
+    B_CUDA(cudaMalloc(&b->p_phi, phi.size() * sizeof(int4)));
+    B_CUDA(cudaMalloc(&b->p_adam, adam.size() * sizeof(int2)));
+    B_CUDA(cudaMemcpy(b->p_warps, warps.data(), warps.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    B_CUDA(cudaMemcpy(b->p_phi, phi.data(), phi.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    B_CUDA(cudaMemcpy(b->p_adam, adam.data(), adam.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    B_CUDA(cudaMemcpy(b->p_need, need.data(), need.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    stamp::PersistArgs& pa = b->pa;
+    pa.inst = b->p_inst;
+    pa.sinst = b->sinst;
+    pa.need = b->p_need;
+    pa.warps = b->p_warps;
+    pa.pw = b->pw_items;
+    pa.med = b->med_items;
+    pa.phi = b->p_phi;
+    pa.adam = b->p_adam;
+    pa.n_roll = n_roll;
+    pa.n_pw = b->n_pw;
+    pa.n_med = b->n_med;
+    pa.n_phi = (int)phi.size();
+    pa.n_adam = (int)adam.size();
+    pa.n_inst = b->n;
+    pa.active = b->active;
+    pa.iter = b->iter;
+    pa.step = b->step;
+    pa.bc = b->bc;
+    pa.theta = b->theta;
+    pa.m = b->m;
+    pa.v = b->v;
+    pa.ctr = b->p_ctr;
+    pa.dep = b->p_dep;
+    pa.flag = b->flag;
+    pa.dropped = b->dropped;
+    pa.dp = stamp::persist_dp(b->max_D);
+    return STAMP_OK;
+}
+
+// Zero what a Stein iteration expects to find zeroed (histograms, last-CTA
+// counters, the persistent queue and its completion counters): a solve may
+// follow an interrupted one or the other launch mode.
+stamp_status clear_counters(stamp_batch* b) {
+    B_CUDA(cudaMemsetAsync(b->hist, 0, b->hist_bytes, b->st));
+    B_CUDA(cudaMemsetAsync(b->counter, 0, (size_t)b->n * 3 * sizeof(unsigned), b->st));
+    B_CUDA(cudaMemsetAsync(b->p_ctr, 0, 4 * sizeof(unsigned), b->st));
+    B_CUDA(cudaMemsetAsync(b->p_dep, 0, (size_t)b->n * stamp::kPersistDeps * sizeof(unsigned), b->st));
     return STAMP_OK;
 }
 
@@ -325,8 +481,9 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
         delete b;
         return bfail(STAMP_ECUDA, "stream creation failed");
     }
-    // layout: every instance's blocks start on 16-byte boundaries
-    auto al4 = [](long long x) { return (x + 3) / 4 * 4; };
+    // layout: every instance's blocks start on 128-byte boundaries (no cache
+    // line holds two instances' data)
+    auto al32 = [](long long x) { return (x + 31) / 32 * 32; };
     long long e = 0, p = 0, q2 = 0, c0 = 0, t0 = 0;
     b->D.resize(n_instances);
     for (int g = 0; g < n_instances; ++g) {
@@ -337,15 +494,15 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
         int shares, jc;
         stamp::phi_batch_plan(d.N, &shares, &jc);
         b->elem0.push_back(e);
-        e += al4((long long)d.N * D);
+        e += al32((long long)d.N * D);
         b->part0.push_back(p);
-        p += al4((long long)shares * d.N * D);
+        p += al32((long long)shares * d.N * D);
         b->d20.push_back(q2);
-        q2 += (long long)d.N * d.N;
+        q2 += al32((long long)d.N * d.N);
         b->cost0.push_back(c0);
-        c0 += d.N;
+        c0 += al32(d.N);
         b->tape0.push_back(t0);
-        t0 += al4((long long)(d.H * phys.T + 1) * d.N * 6 * d.n_blocks);   // room for any C
+        t0 += al32((long long)(d.H * phys.T + 1) * d.N * 6 * d.n_blocks);   // room for any C
     }
     b->n_elem = e;
     const long long hist_n = (long long)n_instances * (2048 + 2048 + 1024);
@@ -362,6 +519,10 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
         {(void**)&b->nvec, n_instances * 4}, {(void**)&b->cost0_dev, n_instances * 8},
         {(void**)&b->dropped, 8}, {(void**)&b->sinst, n_instances * sizeof(SvgdInst)},
         {(void**)&b->bc, (size_t)(kMaxIters + 1) * sizeof(float2)},
+        {(void**)&b->p_inst, n_instances * sizeof(BatchInst)},
+        {(void**)&b->p_need, n_instances * sizeof(int4)},
+        {(void**)&b->p_ctr, 4 * sizeof(unsigned)},
+        {(void**)&b->p_dep, (size_t)n_instances * stamp::kPersistDeps * sizeof(unsigned)},
     };
     size_t total = 0;
     for (const Part& q : parts) total += (q.bytes + 255) / 256 * 256;
@@ -429,6 +590,7 @@ stamp_status stamp_batch_create(const stamp_problem_desc* physics, const stamp_i
         B_CUDA(cudaMemcpy(b->pw_items, pw.data(), pw.size() * sizeof(int4), cudaMemcpyHostToDevice));
         B_CUDA(cudaMemcpy(b->med_items, med.data(), med.size() * sizeof(int2), cudaMemcpyHostToDevice));
         B_CUDA(cudaMemcpy(b->phi_items, phi.data(), phi.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        B_TRY(build_persist_queue(b, si));
         // block-count classes with the single-problem defaults
         for (int nb = 1; nb <= stamp::kMaxBlocks; ++nb) {
             Class c;
@@ -468,6 +630,9 @@ void stamp_batch_destroy(stamp_batch* b) {
     cudaFree(b->pw_items);
     cudaFree(b->med_items);
     cudaFree(b->phi_items);
+    cudaFree(b->p_warps);
+    cudaFree(b->p_phi);
+    cudaFree(b->p_adam);
     cudaFree(b->arena);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -504,6 +669,56 @@ stamp_status stamp_batch_get_config(stamp_batch* b, int n_blocks, int* lanes, in
         }
     return bfail(STAMP_EINVAL, "no instance has %d blocks", n_blocks);
 }
+
+}  // extern "C"
+
+namespace {
+
+// Launch mode: whole Stein iterations (every instance active, no graph) in
+// the per-class launches with the tuned configurations and in the persistent
+// launch; keeps the faster.  The particles are put back afterwards.
+stamp_status tune_mode(stamp_batch* b, int reps, cudaEvent_t e0, cudaEvent_t e1) {
+    float* save = nullptr;
+    B_CUDA(cudaMalloc(&save, (size_t)b->n_elem * sizeof(float)));
+    stamp_status r = STAMP_OK;
+    float ms[2] = {INFINITY, INFINITY};
+    auto run = [&]() -> stamp_status {
+        B_CUDA(cudaMemcpyAsync(save, b->theta, (size_t)b->n_elem * sizeof(float), cudaMemcpyDeviceToDevice, b->st));
+        for (int mode = 0; mode < 2; ++mode) {
+            b->persist = mode == 1;
+            if (b->persist) B_TRY(ensure_persist(b));
+            B_CUDA(cudaMemcpyAsync(b->theta, save, (size_t)b->n_elem * sizeof(float), cudaMemcpyDeviceToDevice, b->st));
+            B_CUDA(cudaMemsetAsync(b->m, 0, b->n_elem * 4, b->st));
+            B_CUDA(cudaMemsetAsync(b->v, 0, b->n_elem * 4, b->st));
+            B_CUDA(cudaMemsetAsync(b->iter, 0, sizeof(int), b->st));
+            B_CUDA(cudaMemsetAsync(b->step, 0, sizeof(int), b->st));
+            B_TRY(clear_counters(b));
+            for (int q = 0; q <= reps; ++q) {
+                if (q == 1) B_CUDA(cudaEventRecord(e0, b->st));   // the first pass warms up
+                B_TRY(iteration(b, b->st));
+            }
+            B_CUDA(cudaEventRecord(e1, b->st));
+            B_CUDA(cudaEventSynchronize(e1));
+            B_CUDA(cudaEventElapsedTime(&ms[mode], e0, e1));
+        }
+        B_CUDA(cudaMemcpyAsync(b->theta, save, (size_t)b->n_elem * sizeof(float), cudaMemcpyDeviceToDevice, b->st));
+        B_CUDA(cudaMemsetAsync(b->flag, 0, sizeof(int), b->st));
+        B_CUDA(cudaStreamSynchronize(b->st));
+        return STAMP_OK;
+    };
+    r = run();
+    cudaStreamSynchronize(b->st);
+    cudaFree(save);
+    b->persist = ms[1] < ms[0];
+    b->mode_ms[0] = ms[0] / reps;
+    b->mode_ms[1] = ms[1] / reps;
+    b->graph_dirty = true;
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
 
 // Autotuner: for every block-count class, time the forward + adjoint launch
 // of the class (CUDA events on the batch's stream; the particles are the
@@ -570,6 +785,7 @@ stamp_status stamp_batch_autotune(stamp_batch* b, int reps) {
         c.C = best_c;
         if ((r = build_class_tables(b, c)) != STAMP_OK) break;
     }
+    if (r == STAMP_OK) r = tune_mode(b, reps, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r == STAMP_OK) B_CUDA(cudaStreamSynchronize(b->st));
@@ -596,6 +812,8 @@ stamp_status stamp_batch_solve(stamp_batch* b, int iters, float lr, float target
     B_CUDA(cudaMemsetAsync(b->flag, 0, sizeof(int), b->st));
     std::vector<int> act(b->n, 1);
     B_CUDA(cudaMemcpyAsync(b->active, act.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->st));
+    B_TRY(clear_counters(b));
+    if (b->persist) B_TRY(ensure_persist(b));
     b->iters_done.assign(b->n, iters);
     b->best.assign(b->n, INFINITY);
     b->tts.assign(b->n, -1.0);
@@ -652,6 +870,11 @@ stamp_status stamp_batch_solve(stamp_batch* b, int iters, float lr, float target
     B_CUDA(cudaStreamSynchronize(b->st));
     b->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     for (int g = 0; g < b->n; ++g) b->best[g] = mins[g];
+    if (b->extra_wait) {   // the injected wait failure lasts one solve
+        b->extra_wait = 0;
+        b->wait_ns = kWaitNs;
+        b->graph_dirty = true;
+    }
     if (flag & 2) return bfail(STAMP_ETIMEOUT, "a bounded device wait gave up");
     if (flag & 1) return bfail(STAMP_ENONFINITE, "a non-finite particle or Stein direction was produced");
     return STAMP_OK;
@@ -688,6 +911,29 @@ stamp_status stamp_batch_screen(stamp_batch* b, stamp_surrogate* s, int g, int n
     return STAMP_OK;
 }
 
+stamp_status stamp_batch_set_persistent(stamp_batch* b, int on) {
+    if (!b) return bfail(STAMP_EINVAL, "NULL batch");
+    if ((on != 0) != b->persist) b->graph_dirty = true;
+    b->persist = on != 0;
+    return STAMP_OK;
+}
+
+stamp_status stamp_batch_get_persistent(stamp_batch* b, int* on, float* ms_per_class, float* ms_persistent) {
+    if (!b) return bfail(STAMP_EINVAL, "NULL batch");
+    if (on) *on = b->persist ? 1 : 0;
+    if (ms_per_class) *ms_per_class = b->mode_ms[0];
+    if (ms_persistent) *ms_persistent = b->mode_ms[1];
+    return STAMP_OK;
+}
+
+stamp_status stamp_batch_inject_wait_timeout(stamp_batch* b) {
+    if (!b) return bfail(STAMP_EINVAL, "NULL batch");
+    b->extra_wait = 1;
+    b->wait_ns = 2000000ull;   // 2 ms
+    b->graph_dirty = true;
+    return STAMP_OK;
+}
+
 stamp_status stamp_batch_results(stamp_batch* b, int* iterations, float* best_cost, double* seconds_to_target,
                                  int* top3, long long* units, double* seconds) {
     if (!b) return bfail(STAMP_EINVAL, "NULL batch");
@@ -710,6 +956,14 @@ stamp_status stamp_batch_results(stamp_batch* b, int* iterations, float* best_co
 stamp_status stamp_batch_read_theta(stamp_batch* b, int instance, float* theta_out) {
     if (!b || instance < 0 || instance >= b->n || !theta_out) return bfail(STAMP_EINVAL, "bad arguments");
     B_CUDA(cudaMemcpy(theta_out, b->theta + b->elem0[instance],
+                      (size_t)b->inst[instance].N * b->D[instance] * sizeof(float), cudaMemcpyDefault));
+    return STAMP_OK;
+}
+
+stamp_status stamp_batch_read_grad(stamp_batch* b, int instance, float* grad_out) {
+    if (!b || instance < 0 || instance >= b->n || !grad_out) return bfail(STAMP_EINVAL, "bad arguments");
+    B_CUDA(cudaStreamSynchronize(b->st));
+    B_CUDA(cudaMemcpy(grad_out, b->grad + b->elem0[instance],
                       (size_t)b->inst[instance].N * b->D[instance] * sizeof(float), cudaMemcpyDefault));
     return STAMP_OK;
 }

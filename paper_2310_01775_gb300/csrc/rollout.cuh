@@ -436,6 +436,14 @@ __device__ __forceinline__ void load_state(const float2* src, Blocks<NB>& s) {
     for (int q = 0; q < 3 * NB; ++q) set_chunk(s, q, src[q]);
 }
 
+// The same through L2 only: for a tape that other lanes of the warp wrote
+// earlier in the same launch (no non-coherent cache line can be stale).
+template <int NB>
+__device__ __forceinline__ void load_state_cg(const float2* src, Blocks<NB>& s) {
+#pragma unroll
+    for (int q = 0; q < 3 * NB; ++q) set_chunk(s, q, __ldcg(src + q));
+}
+
 template <int NB>
 __device__ __forceinline__ void init_state(const SimConst& sc, Blocks<NB>& s) {
 #pragma unroll
@@ -846,16 +854,20 @@ __device__ __forceinline__ void substep_vjp(const SimConst& sc, const Blocks<NB>
 }
 
 // ------------------------------ adjoint kernel --------------------------------
-// Shared memory: per team, C states (before each substep of the current
-// segment), stride C*S/2 + 1 float2 to spread teams over banks.
-template <int NB, int L>
+// seg: the team's shared memory, C states (before each substep of the current
+// segment) when C > 1; teams sit seg_stride<NB>(C) float2 apart to spread
+// them over banks.
+template <int NB>
+__host__ __device__ constexpr int seg_stride(int C) { return C * (Dims<NB>::S / 2) + 1; }
+
+// kL2: read the tape through L2 only (a forward of the same launch wrote it).
+template <int NB, int L, bool kL2 = false>
 __device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& a, int i, bool on,
-                                         int lane) {
+                                         int lane, float2* seg) {
     constexpr int M = Dims<NB>::M, P = Dims<NB>::P, S = Dims<NB>::S, SP = Slots<NB, L>::SP;
-    extern __shared__ float2 seg_smem[];
-    const int team = threadIdx.x / L;
-    const int seg_stride = sc.C * (S / 2) + 1;
-    float2* seg = seg_smem + (size_t)team * seg_stride;
+    auto load_tape = [](const float2* src, Blocks<NB>& st) {
+        if constexpr (kL2) load_state_cg(src, st); else load_state(src, st);
+    };
     const float* th = a.theta + (size_t)i * sc.D;
     float* gr = a.grad + (size_t)i * sc.D;
     const bool noise = a.iter >= 0;
@@ -867,7 +879,7 @@ __device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& 
     Corners<NB, L> cn;
     make_corners(cn, lane);
     Blocks<NB> s, adj;
-    load_state(tape_i + (size_t)sc.n_ckpt * ck2, s);
+    load_tape(tape_i + (size_t)sc.n_ckpt * ck2, s);
     zero(adj);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -880,7 +892,7 @@ __device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& 
     bool bad = false;
     for (int k = sc.H - 1; k >= 0; --k) {
         Blocks<NB> s0;
-        load_state(tape_i + (size_t)(k * segs) * ck2, s0);
+        load_tape(tape_i + (size_t)(k * segs) * ck2, s0);
         float z[M], uu, vv;
         relax_action<NB>(sc, th, k, i + a.particle0, gkey, noise, hard, z, uu, vv);
         const float tu = tanhf(uu);
@@ -894,7 +906,7 @@ __device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& 
         for (int q = 0; q < SP; ++q) acc.p0x[q] = acc.p0y[q] = acc.dx[q] = acc.dy[q] = acc.w[q] = 0.f;
 
         Blocks<NB> nxt;
-        load_state(tape_i + (size_t)(k * segs + segs - 1) * ck2, nxt);
+        load_tape(tape_i + (size_t)(k * segs + segs - 1) * ck2, nxt);
         // with a replayed tape, the yaws' (cos, sin) come with the states
         const bool have_trig = sc.C == 1 && a.trig != nullptr;
         const size_t ckt = (size_t)a.N * NB;                         // float2 per trig row
@@ -911,7 +923,7 @@ __device__ __forceinline__ void adj_team(const SimConst& sc, const RolloutArgs& 
             // segment (nothing here touches it before the next iteration: warps
             // issue in order, so an early use would stall on the load)
             if (sgi > 0) {
-                load_state(tape_i + (size_t)(k * segs + sgi - 1) * ck2, nxt);
+                load_tape(tape_i + (size_t)(k * segs + sgi - 1) * ck2, nxt);
                 if (have_trig) load_trig<NB>(trig_i + (size_t)(k * segs + sgi - 1) * ckt, ncs, nsn);
             }
             if (sc.C == 1) {   // every state is on the tape: nothing to recompute
@@ -1022,7 +1034,9 @@ __global__ void __launch_bounds__(128) rollout_adj_kernel(const SimConst sc, con
     int i = gtid / L;
     const bool on = i < a.N;
     if (!on) i = a.N - 1;
-    adj_team<NB, L>(sc, a, i, on, gtid & (L - 1));
+    extern __shared__ float2 seg_smem[];
+    adj_team<NB, L>(sc, a, i, on, gtid & (L - 1),
+                    seg_smem + (size_t)(threadIdx.x / L) * seg_stride<NB>(sc.C));
 }
 
 template <int NB, int L>
@@ -1033,7 +1047,9 @@ __global__ void __launch_bounds__(128) rollout_adj_batch_kernel(const SimConst s
     int i;
     bool on;
     if (!batch_team<NB>(sc0, b, gtid / L, sc, a, i, on)) return;
-    adj_team<NB, L>(sc, a, i, on, gtid & (L - 1));
+    extern __shared__ float2 seg_smem[];
+    adj_team<NB, L>(sc, a, i, on, gtid & (L - 1),
+                    seg_smem + (size_t)(threadIdx.x / L) * seg_stride<NB>(sc.C));
 }
 
 // ------------------------------ segment replay --------------------------------

@@ -222,6 +222,55 @@ int phi_rows_per_block();
 cudaError_t launch_topk(const float* theta, const float* cost, int N, const SimConst& sc, int k,
                         int* topk_out, cudaStream_t st);
 
+// Persistent batched iteration (batch_persist.cu): one launch runs a whole
+// Stein iteration of every active instance.  Each CTA of kPersistThreads
+// takes work items from a device-wide queue in this order -- rollout items
+// (kPersistWarps warp tasks: forward, then adjoint, of up to 32/L particles
+// of one instance), pairwise tiles, median-digit-1 CTAs, median-digit-2
+// CTAs, Stein-direction blocks, Adam chunks -- and waits (bounded) only on
+// items of the same instance earlier in the queue.
+constexpr int kPersistThreads = 256;
+constexpr int kPersistWarps = kPersistThreads / 32;
+constexpr int kPersistRows = kPersistWarps * 4;   // Stein-direction rows per item
+constexpr int kPersistAdamChunk = 4096;           // particle elements per Adam item
+constexpr int kPersistDeps = 5;                   // completion counters per instance
+// lanes per particle team in the persistent kernel, by block count
+__host__ __device__ constexpr int persist_lanes(int nb) { return nb == 1 ? 2 : nb == 2 ? 4 : 8; }
+// Stein-direction column slots per lane for the batch's largest D
+__host__ __device__ constexpr int persist_dp(int max_D) { return max_D <= 96 ? 3 : max_D <= 192 ? 6 : 9; }
+struct PersistArgs {
+    const BatchInst* inst;  // per batch instance (n_ckpt of its class's interval)
+    const SvgdInst* sinst;  // per batch instance
+    const int4* need;       // per instance: rollout warps, pairwise tiles, median CTAs, Stein items
+    const int4* warps;      // kPersistWarps per rollout item: (instance or -1, first particle, n_blocks, 0)
+    const int4* pw;         // (instance, tile row, tile column, 0)
+    const int2* med;        // (instance, CTA), for both median digits
+    const int4* phi;        // (instance, row block of kPersistRows, j-share, 0)
+    const int2* adam;       // (instance, chunk)
+    int n_roll, n_pw, n_med, n_phi, n_adam, n_inst;
+    const int* active;
+    int* iter;              // Stein iterations so far (Gumbel key); the last CTA out bumps it
+    int* step;              // Adam steps so far; likewise
+    const float2* bc;       // Adam bias corrections by step
+    float lr;
+    float *theta, *m, *v;   // the batch's concatenated particles and Adam moments
+    unsigned* ctr;          // [0] next item, [1] CTAs finished, [2] abort; zero between launches
+    unsigned* dep;          // kPersistDeps per instance, zero between launches: rollout warps,
+                            // pairwise tiles, median-1 CTAs, median-2 CTAs, Stein items done
+    int* flag;              // bit 0: non-finite; bit 1: a bounded wait gave up
+    unsigned long long* dropped;
+    int seg_warp;           // float2 of shared memory per warp for the adjoint's segments
+    int dp;                 // Stein-direction column slots per lane: 3, 6 or 9
+    int extra_wait;         // added to the Stein items' rollout target (> 0: a wait that runs out)
+    unsigned long long wait_ns;   // a dependency wait gives up after this long
+};
+// Dynamic shared memory the launch needs, and the grid (all resident CTAs).
+size_t persist_smem(int max_D, int seg_warp);
+cudaError_t persist_grid(size_t smem, int* grid);
+// cls[nb - 1]: the constants of the n_blocks = nb class (unused classes: anything).
+cudaError_t launch_persist(const PersistArgs& p, const SimConst* cls, int grid, size_t smem,
+                           cudaStream_t st);
+
 // Problem constants of a problem object, and a forward rollout (timed like
 // the solve's) from per-particle start poses (N x n_blocks x 3, at rest).
 SimConst problem_const(const stamp_problem* p);

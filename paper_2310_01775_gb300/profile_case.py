@@ -3,6 +3,7 @@
     python -m paper_2310_01775_gb300.profile_case pusher1_h4 20
     python -m paper_2310_01775_gb300.profile_case surrogate 20
     python -m paper_2310_01775_gb300.profile_case batch 20      # or batch64: first 64 instances
+    python -m paper_2310_01775_gb300.profile_case pbatch 20     # the same, persistent launch
     python -m paper_2310_01775_gb300.profile_case structured 20  # or dsvgd: pusher1_h4 variants
 
 Builds the workload's problem (seed 0 scene), runs `iters` SVGD iterations
@@ -45,15 +46,16 @@ def surrogate_case(iters: int) -> float:
     return float(cost.min())
 
 
-def batch_case(iters: int, n: int = 256) -> float:
+def batch_case(iters: int, n: int = 256, persistent: bool = False) -> float:
     """The first n of the 256 seeded serving instances (uniform goals), with the
     launch configuration the autotuner picks on GB300, `iters` iterations
-    launched one by one."""
+    launched one by one (persistent: one launch per iteration)."""
     insts = W.batch_instances(256)[:n]
     b = S.Batch(dict(W.PHYSICS, T=100), insts, torch.cuda.current_stream().cuda_stream)
     for nb, cfg in {1: (2, 64, 1), 2: (4, 128, 1), 3: (8, 128, 1), 4: (8, 128, 1)}.items():
         if any(d["n_blocks"] == nb for d in insts):
             b.set_config(nb, *cfg)
+    b.set_persistent(persistent)
     b.solve(iters, 1e-2, use_graph=False)
     best = float(b.results()["best_cost"].min())
     b.close()
@@ -84,6 +86,8 @@ def main(name: str = "pusher1_h4", iters: int = 2) -> float:
         return surrogate_case(iters)
     if name.startswith("batch"):
         return batch_case(iters, int(name[5:] or 256))
+    if name.startswith("pbatch"):
+        return batch_case(iters, int(name[6:] or 256), persistent=True)
     P = W.params(name)
     init, goal = W.scene(P, 0)
     N = P["N"]

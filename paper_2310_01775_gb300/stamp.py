@@ -107,6 +107,10 @@ _sigs = {
     "stamp_svgd_step_rows": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _f, _i, _vp, _vp],
     "stamp_batch_screen": [_vp, _vp, _i, _i],
     "stamp_set_replay_lanes": [_vp, _i],
+    "stamp_batch_set_persistent": [_vp, _i],
+    "stamp_batch_get_persistent": [_vp, _vp, _vp, _vp],
+    "stamp_batch_inject_wait_timeout": [_vp],
+    "stamp_batch_read_grad": [_vp, _i, _vp],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -569,6 +573,21 @@ class Batch:
     def autotune(self, reps=2):
         _check(_lib.stamp_batch_autotune(self.handle, reps))
 
+    def set_persistent(self, on: bool):
+        """One launch per Stein iteration (True) or the per-class launches."""
+        _check(_lib.stamp_batch_set_persistent(self.handle, int(bool(on))))
+
+    def persistent(self) -> tuple[bool, float, float]:
+        """(launch mode, autotuned ms per iteration per-class, persistent)."""
+        on, a, p = ctypes.c_int(), ctypes.c_float(), ctypes.c_float()
+        _check(_lib.stamp_batch_get_persistent(self.handle, ctypes.byref(on), ctypes.byref(a),
+                                               ctypes.byref(p)))
+        return bool(on.value), a.value, p.value
+
+    def inject_wait_timeout(self):
+        """The next persistent solve's dependency waits run out (error-path test)."""
+        _check(_lib.stamp_batch_inject_wait_timeout(self.handle))
+
     def solve(self, iters, lr, target_cost=0.0, check_every=0, use_graph=True):
         _check(_lib.stamp_batch_solve(self.handle, iters, lr, target_cost, check_every,
                                       int(use_graph)))
@@ -593,3 +612,7 @@ class Batch:
 
     def read_theta(self, instance, out):
         _check(_lib.stamp_batch_read_theta(self.handle, instance, _f32(out, "theta_out")))
+
+    def read_grad(self, instance, out):
+        """grad log rho (N x D) of the instance's last Stein iteration."""
+        _check(_lib.stamp_batch_read_grad(self.handle, instance, _f32(out, "grad_out")))
