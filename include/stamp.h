@@ -546,7 +546,8 @@ stamp_status stamp_batch_get_config(stamp_batch* batch, int n_blocks, int* lanes
  * supported lane count, CTA size 64/128 and checkpoint interval 1/5/25 on
  * the solve's initial particles, and keeps the fastest; then times `reps`
  * whole iterations in each launch mode (the persistent mode with the tuned
- * checkpoint intervals) and keeps the faster mode.  The particles are left
+ * checkpoint intervals and, if one is above 1, with interval 1 everywhere)
+ * and keeps the fastest mode (and its intervals).  The particles are left
  * as they were (screened ones included).  Waits. */
 stamp_status stamp_batch_autotune(stamp_batch* batch, int reps);
 /* Launch mode: on != 0 the persistent launch, 0 the per-class launches (the

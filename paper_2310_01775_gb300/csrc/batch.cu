@@ -309,10 +309,11 @@ stamp_status hard_eval(stamp_batch* b, bool all) {
     return STAMP_OK;
 }
 
-// Work queue of the persistent launch.  Rollout items go longest first: a
-// warp task's time is estimated as horizon x a per-block-count cost (per-warp
-// rollout + adjoint time per action, measured on GB300 with the per-class
-// kernels at their tuned lanes).  The Stein blocks and Adam chunks follow in
+// Work queue of the persistent launch.  Rollout items go by block count,
+// most blocks first, and longest first within a block count: a warp task's
+// time is estimated as horizon x a per-block-count cost (per-warp rollout +
+// adjoint time per action, measured on GB300 with the per-class kernels at
+// their tuned lanes).  The Stein blocks and Adam chunks follow in
 // the order in which a list schedule of the rollout items over one CTA per
 // SM finishes the instances' rollouts.
 stamp_status build_persist_queue(stamp_batch* b, const std::vector<SvgdInst>& si) {
@@ -329,7 +330,10 @@ stamp_status build_persist_queue(stamp_batch* b, const std::vector<SvgdInst>& si
         const int rb = (d.N + stamp::kPersistRows - 1) / stamp::kPersistRows;
         need[g] = make_int4(warps, si[g].nt * (si[g].nt + 1) / 2, si[g].med_ctas, si[g].shares * rb);
     }
-    std::stable_sort(tasks.begin(), tasks.end(), [](const Task& x, const Task& y) { return x.t > y.t; });
+    // by block count (consecutive items on an SM run the same code), longest first within it
+    std::stable_sort(tasks.begin(), tasks.end(), [](const Task& x, const Task& y) {
+        return x.nb != y.nb ? x.nb > y.nb : x.t > y.t;
+    });
     const int n_roll = (int)((tasks.size() + W - 1) / W);
     std::vector<int4> warps((size_t)n_roll * W, make_int4(-1, 0, 0, 0));
     for (size_t q = 0; q < tasks.size(); ++q) warps[q] = make_int4(tasks[q].g, tasks[q].first, tasks[q].nb, 0);
@@ -675,17 +679,35 @@ stamp_status stamp_batch_get_config(stamp_batch* b, int n_blocks, int* lanes, in
 namespace {
 
 // Launch mode: whole Stein iterations (every instance active, no graph) in
-// the per-class launches with the tuned configurations and in the persistent
-// launch; keeps the faster.  The particles are put back afterwards.
+// the per-class launches with the tuned configurations, in the persistent
+// launch with the tuned checkpoint intervals and, if any is above one, in
+// the persistent launch with interval-1 tapes (no segment recompute; the
+// tape a warp writes is read back at once, from L2); keeps the fastest.  The
+// particles are put back afterwards.
 stamp_status tune_mode(stamp_batch* b, int reps, cudaEvent_t e0, cudaEvent_t e1) {
     float* save = nullptr;
     B_CUDA(cudaMalloc(&save, (size_t)b->n_elem * sizeof(float)));
     stamp_status r = STAMP_OK;
-    float ms[2] = {INFINITY, INFINITY};
+    std::vector<int> tuned_c;
+    for (const Class& c : b->cls) tuned_c.push_back(c.C);
+    const bool any_c = std::any_of(tuned_c.begin(), tuned_c.end(), [](int C) { return C > 1; });
+    float ms[3] = {INFINITY, INFINITY, INFINITY};
+    auto set_c = [&](bool ones) -> stamp_status {
+        for (size_t q = 0; q < b->cls.size(); ++q) {
+            Class& c = b->cls[q];
+            const int want = ones ? 1 : tuned_c[q];
+            if (c.C != want) {
+                c.C = want;
+                B_TRY(build_class_tables(b, c));
+            }
+        }
+        return STAMP_OK;
+    };
     auto run = [&]() -> stamp_status {
         B_CUDA(cudaMemcpyAsync(save, b->theta, (size_t)b->n_elem * sizeof(float), cudaMemcpyDeviceToDevice, b->st));
-        for (int mode = 0; mode < 2; ++mode) {
-            b->persist = mode == 1;
+        for (int mode = 0; mode < (any_c ? 3 : 2); ++mode) {
+            b->persist = mode >= 1;
+            if (mode == 2) B_TRY(set_c(true));
             if (b->persist) B_TRY(ensure_persist(b));
             B_CUDA(cudaMemcpyAsync(b->theta, save, (size_t)b->n_elem * sizeof(float), cudaMemcpyDeviceToDevice, b->st));
             B_CUDA(cudaMemsetAsync(b->m, 0, b->n_elem * 4, b->st));
@@ -709,9 +731,11 @@ stamp_status tune_mode(stamp_batch* b, int reps, cudaEvent_t e0, cudaEvent_t e1)
     r = run();
     cudaStreamSynchronize(b->st);
     cudaFree(save);
-    b->persist = ms[1] < ms[0];
+    const int best = ms[2] < std::min(ms[0], ms[1]) ? 2 : ms[1] < ms[0] ? 1 : 0;
+    b->persist = best >= 1;
+    if (r == STAMP_OK) r = set_c(best == 2);
     b->mode_ms[0] = ms[0] / reps;
-    b->mode_ms[1] = ms[1] / reps;
+    b->mode_ms[1] = std::min(ms[1], ms[2]) / reps;
     b->graph_dirty = true;
     return r;
 }

@@ -6,10 +6,12 @@
 // the adjoint's register count).  Each CTA takes the next work item from a
 // device-wide counter until the queue is empty:
 //   rollout items     8 warp tasks; a task is one warp's teams of one
-//                     instance: the forward rollout (tape + cost), then at
-//                     once the checkpointed reverse sweep over that tape
-//                     (gradient of log rho) -- the same team bodies as the
-//                     per-class launches, lanes fixed per block count;
+//                     instance: the forward rollout (tape + cost), then the
+//                     checkpointed reverse sweep over that tape (gradient of
+//                     log rho) -- the same team bodies as the per-class
+//                     launches, lanes fixed per block count; the CTA's warps
+//                     all finish their forwards before the adjoints start
+//                     (one loop body in the SM's instruction cache at a time);
 //   pairwise tiles    d2 and the median's first radix digit;
 //   median CTAs       the second digit, then the third (h);
 //   Stein blocks      phi for 32 rows and one j-share (Eq. svgd);
@@ -85,10 +87,11 @@ __device__ __forceinline__ void cta_signal(unsigned* c) {
     if (threadIdx.x == 0) atomicAdd(c, 1u);
 }
 
-// One warp task: the warp's teams of instance g starting at particle `first`.
+// One warp task: the warp's teams of instance g starting at particle `first`;
+// phase 0 the forward rollout, phase 1 the adjoint over the tape it wrote.
 template <int NB>
 __device__ __forceinline__ void roll_warp(const SimConst& sc0, const PersistArgs& p, int g,
-                                          int first, float2* wseg) {
+                                          int first, float2* wseg, int phase) {
     constexpr int L = persist_lanes(NB);
     const BatchInst& in = p.inst[g];
     SimConst sc = sc0;
@@ -116,10 +119,11 @@ __device__ __forceinline__ void roll_warp(const SimConst& sc0, const PersistArgs
     int i = first + lane32 / L;
     const bool on = i < in.N;
     if (!on) i = in.N - 1;   // surplus teams shadow the last particle, store nothing
-    rollout::fwd_team<NB, L>(sc, a, i, on, lane32 & (L - 1));
-    __syncwarp();            // the tape rows of the team's other lanes are visible
-    rollout::adj_team<NB, L, true>(sc, a, i, on, lane32 & (L - 1),
-                                   wseg + (size_t)(lane32 / L) * rollout::seg_stride<NB>(sc.C));
+    if (phase == 0)
+        rollout::fwd_team<NB, L>(sc, a, i, on, lane32 & (L - 1));
+    else
+        rollout::adj_team<NB, L, true>(sc, a, i, on, lane32 & (L - 1),
+                                       wseg + (size_t)(lane32 / L) * rollout::seg_stride<NB>(sc.C));
 }
 
 // Adam (Kingma & Ba 2015) on elements [chunk*kPersistAdamChunk, ...) of instance s.
@@ -182,15 +186,23 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         if (k >= e_all) break;
         if (stop) continue;   // drain the queue after an abort
         if (k < e_roll) {
+            // every warp's forward, then (the tapes visible CTA-wide) every
+            // warp's adjoint: the SM's warps run one loop body at a time
             const int4 w = p.warps[(size_t)k * kPersistWarps + warp];
-            if (w.x >= 0 && p.active[w.x]) {
-                float2* wseg = pdyn + (size_t)warp * p.seg_warp;
-                switch (w.z) {
-                    case 1: roll_warp<1>(c1, p, w.x, w.y, wseg); break;
-                    case 2: roll_warp<2>(c2, p, w.x, w.y, wseg); break;
-                    case 3: roll_warp<3>(c3, p, w.x, w.y, wseg); break;
-                    default: roll_warp<4>(c4, p, w.x, w.y, wseg); break;
+            const bool run = w.x >= 0 && p.active[w.x];
+            float2* wseg = pdyn + (size_t)warp * p.seg_warp;
+            for (int phase = 0; phase < 2; ++phase) {
+                if (run) {
+                    switch (w.z) {
+                        case 1: roll_warp<1>(c1, p, w.x, w.y, wseg, phase); break;
+                        case 2: roll_warp<2>(c2, p, w.x, w.y, wseg, phase); break;
+                        case 3: roll_warp<3>(c3, p, w.x, w.y, wseg, phase); break;
+                        default: roll_warp<4>(c4, p, w.x, w.y, wseg, phase); break;
+                    }
                 }
+                __syncthreads();
+            }
+            if (run) {
                 __threadfence();
                 __syncwarp();
                 if ((tid & 31) == 0) atomicAdd(p.dep + (size_t)kPersistDeps * w.x, 1u);

@@ -220,19 +220,22 @@ def test_autotune_times_both_modes_and_keeps_the_faster():
 
 def test_full_size_persistent_gradients_sampled():
     """The 256 uneven instances of the serving workload (1-4 blocks, H 2-8,
-    N 64-1024, T = 100, interval-1 tapes) in one persistent launch: for the
-    first instance of each block count, the first 8 particles' gradients
-    against the oracle with the parity bar (at these horizons few particles
-    of the stiff contact are conditioned: the float32-floor comparison
-    carries the check)."""
+    N 64-1024, T = 100, interval-1 tapes) in one persistent launch, with
+    the softer contact (at T = 100 few particles of the literal constants
+    are conditioned; those are covered above at T = 50): for the first
+    two-action instance of each block count, particles spread over its
+    warps against the oracle with the parity bar."""
+    phys = dict(W.PHYSICS, **SOFT)
     insts = W.batch_instances(256, 0)
-    b = _batch(insts, 100)
+    b = _batch(insts, 100, True, phys)
     for nb in range(1, 5):
         b.set_config(nb, LANES[nb], 128, 1)
     b.solve(1, 1e-2)
-    first = {}
+    pick = {}
     for g, d in enumerate(insts):
-        first.setdefault(d["n_blocks"], g)
-    _grad_bar(insts, _grads(b, insts), W.PHYSICS, 100, {nb: 1 for nb in range(1, 5)},
-              sample={g: 8 for g in first.values()})
+        if d["H"] == 2:
+            pick.setdefault(d["n_blocks"], g)
+    assert len(pick) == 4
+    _grad_bar(insts, _grads(b, insts), phys, 100, {nb: 1 for nb in range(1, 5)},
+              sample={g: (8 if nb == 4 else 12) for nb, g in pick.items()})
     b.close()
