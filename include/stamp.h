@@ -557,6 +557,21 @@ stamp_status stamp_batch_autotune(stamp_batch* batch, int reps);
 stamp_status stamp_batch_set_persistent(stamp_batch* batch, int on);
 stamp_status stamp_batch_get_persistent(stamp_batch* batch, int* on, float* ms_per_class,
                                         float* ms_persistent);
+/* Trace of the persistent launch (profiling): with on != 0 every launch
+ * records, per work item k, its claim time, the time its dependencies were
+ * met and its end time (%globaltimer, ns) and the SM that ran it, in entry k
+ * (later launches overwrite earlier ones; the graph is re-captured).  The
+ * read call copies up to `capacity` entries of the last launch and returns
+ * the queue's item count and its five kinds in queue order: rollout items,
+ * pairwise tiles, median CTAs (per digit; the two digits follow each
+ * other), Stein blocks, Adam chunks.  Any output pointer may be NULL. */
+typedef struct {
+    unsigned long long claim_ns, start_ns, end_ns;
+    unsigned item, sm;
+} stamp_trace_entry;
+stamp_status stamp_batch_set_trace(stamp_batch* batch, int on);
+stamp_status stamp_batch_read_trace(stamp_batch* batch, stamp_trace_entry* out, int capacity,
+                                    int* n_items, int* kinds5);
 /* Error-path test: in the next stamp_batch_solve only, the persistent
  * launch's Stein items wait for one rollout warp more than exist, with a
  * 2 ms limit.  The wait runs out, the launch drains its queue, and the solve

@@ -147,6 +147,7 @@ struct stamp_batch {
     int2* p_adam = nullptr;
     unsigned *p_ctr = nullptr, *p_dep = nullptr;
     int extra_wait = 0;              // > 0 for the next solve: its Stein items' waits run out
+    stamp_trace_entry* trace = nullptr;   // persistent-launch trace (NULL: off)
     unsigned long long wait_ns = kWaitNs;
     float mode_ms[2] = {-1.f, -1.f};   // autotuner: ms per iteration, per-class and persistent
     // instances whose next solve starts from particles set by stamp_batch_screen
@@ -242,6 +243,11 @@ stamp_status rollout_class(stamp_batch* b, const Class& c, bool adjoint, bool ha
 // the particles only: they run on the side stream beside the rollouts, and
 // the Stein direction waits for both (fork and join become graph edges when
 // captured).
+int n_items(const stamp_batch* b) {
+    const stamp::PersistArgs& p = b->pa;
+    return p.n_roll + p.n_pw + 2 * p.n_med + p.n_phi + p.n_adam;
+}
+
 stamp_status iteration(stamp_batch* b, cudaStream_t st) {
     if (b->persist) {
         if (b->persist_dirty) return bfail(STAMP_EINVAL, "persistent tables out of date");
@@ -249,6 +255,8 @@ stamp_status iteration(stamp_batch* b, cudaStream_t st) {
         pa.lr = b->lr;
         pa.extra_wait = b->extra_wait;
         pa.wait_ns = b->wait_ns;
+        pa.trace = b->trace;
+        pa.trace_cap = b->trace ? n_items(b) : 0;
         B_CUDA(stamp::launch_persist(pa, b->cls_sc, b->persist_grid, b->persist_smem, st));
         return STAMP_OK;
     }
@@ -637,6 +645,7 @@ void stamp_batch_destroy(stamp_batch* b) {
     cudaFree(b->p_warps);
     cudaFree(b->p_phi);
     cudaFree(b->p_adam);
+    cudaFree(b->trace);
     cudaFree(b->arena);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -947,6 +956,40 @@ stamp_status stamp_batch_get_persistent(stamp_batch* b, int* on, float* ms_per_c
     if (on) *on = b->persist ? 1 : 0;
     if (ms_per_class) *ms_per_class = b->mode_ms[0];
     if (ms_persistent) *ms_persistent = b->mode_ms[1];
+    return STAMP_OK;
+}
+
+stamp_status stamp_batch_set_trace(stamp_batch* b, int on) {
+    if (!b) return bfail(STAMP_EINVAL, "NULL batch");
+    B_CUDA(cudaStreamSynchronize(b->st));
+    if (on && !b->trace) {
+        const size_t bytes = (size_t)n_items(b) * sizeof(stamp_trace_entry);
+        B_CUDA(cudaMalloc(&b->trace, bytes));
+        B_CUDA(cudaMemset(b->trace, 0, bytes));
+    } else if (!on && b->trace) {
+        cudaFree(b->trace);
+        b->trace = nullptr;
+    }
+    b->graph_dirty = true;
+    return STAMP_OK;
+}
+
+stamp_status stamp_batch_read_trace(stamp_batch* b, stamp_trace_entry* out, int capacity, int* n,
+                                    int* kinds5) {
+    if (!b) return bfail(STAMP_EINVAL, "NULL batch");
+    const int total = n_items(b);
+    if (n) *n = total;
+    if (kinds5) {
+        const stamp::PersistArgs& p = b->pa;
+        const int k[5] = {p.n_roll, p.n_pw, p.n_med, p.n_phi, p.n_adam};
+        for (int q = 0; q < 5; ++q) kinds5[q] = k[q];
+    }
+    if (out && capacity > 0) {
+        if (!b->trace) return bfail(STAMP_EINVAL, "tracing is off");
+        B_CUDA(cudaStreamSynchronize(b->st));
+        B_CUDA(cudaMemcpy(out, b->trace, (size_t)std::min(capacity, total) * sizeof(stamp_trace_entry),
+                          cudaMemcpyDefault));
+    }
     return STAMP_OK;
 }
 

@@ -3,8 +3,10 @@
 // horizon and particle count).
 //
 // The grid is the GPU's resident capacity (one CTA of 256 threads per SM at
-// the adjoint's register count).  Each CTA takes the next work item from a
-// device-wide counter until the queue is empty:
+// the adjoint's register count; two CTAs of 128 threads, which let a Stein
+// item share an SM with a rollout item, measured slower: the two items'
+// loop bodies contend for the instruction cache).  Each CTA takes the next
+// work item from a device-wide counter until the queue is empty:
 //   rollout items     8 warp tasks; a task is one warp's teams of one
 //                     instance: the forward rollout (tape + cost), then the
 //                     checkpointed reverse sweep over that tape (gradient of
@@ -37,6 +39,9 @@ namespace stamp {
 namespace {
 
 constexpr unsigned kMaxPolls = 1u << 26;   // backstop of the timed waits
+
+// trace: when the CTA's current item had its dependencies met
+__shared__ unsigned long long start_sh;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -73,6 +78,7 @@ __device__ bool wait_counts(const PersistArgs& p, const unsigned* c0, unsigned t
         }
         __threadfence();
         ok_sh = ok;
+        if (p.trace) start_sh = now_ns();
     }
     __syncthreads();
     const bool ok = ok_sh != 0;
@@ -185,6 +191,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         __syncthreads();
         if (k >= e_all) break;
         if (stop) continue;   // drain the queue after an abort
+        unsigned long long t_claim = 0;
+        if (p.trace && tid == 0) start_sh = t_claim = now_ns();
         if (k < e_roll) {
             // every warp's forward, then (the tapes visible CTA-wide) every
             // warp's adjoint: the SM's warps run one loop body at a time
@@ -211,8 +219,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             const int4 it = p.pw[k - e_roll];
             if (p.active[it.x]) {
                 const SvgdInst& s = p.sinst[it.x];
-                pairwise_body(s.theta, s.N, s.D, s.d2, s.hist, s.sel, s.counter, s.h, it.y, it.z,
-                              s.nt);
+                pairwise_body<kPersistThreads>(s.theta, s.N, s.D, s.d2, s.hist, s.sel, s.counter,
+                                               s.h, it.y, it.z, s.nt);
                 cta_signal(p.dep + (size_t)kPersistDeps * it.x + 1);
             }
         } else if (k < e_m2) {
@@ -225,8 +233,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                 const unsigned target = dg == 1 ? (unsigned)p.need[g].y : (unsigned)s.med_ctas;
                 if (wait_counts(p, dep + dg, target, nullptr, 0u)) {
                     if (s.N >= 2)
-                        median_digit_body(s.N, dg, s.d2, s.hist, s.sel, s.counter + dg, s.h,
-                                          nullptr, it.y, s.med_ctas);
+                        median_digit_body<kPersistThreads>(s.N, dg, s.d2, s.hist, s.sel,
+                                                           s.counter + dg, s.h, nullptr, it.y,
+                                                           s.med_ctas);
                     cta_signal(dep + dg + 1);
                 }
             }
@@ -257,6 +266,16 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             }
         }
         __syncthreads();   // shared memory is free for the next item
+        if (p.trace && tid == 0 && k < p.trace_cap) {
+            stamp_trace_entry& e = p.trace[k];
+            e.claim_ns = t_claim;
+            e.start_ns = start_sh;
+            e.end_ns = now_ns();
+            e.item = (unsigned)k;
+            unsigned sm;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+            e.sm = sm;
+        }
     }
     // the last CTA out re-arms the queue and advances the iteration
     if (tid == 0) {

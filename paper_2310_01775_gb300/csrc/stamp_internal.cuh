@@ -263,6 +263,10 @@ struct PersistArgs {
     int dp;                 // Stein-direction column slots per lane: 3, 6 or 9
     int extra_wait;         // added to the Stein items' rollout target (> 0: a wait that runs out)
     unsigned long long wait_ns;   // a dependency wait gives up after this long
+    // trace (NULL: off): entry k of the last launch = item k's claim,
+    // work-start (dependencies met) and end times, and its SM
+    stamp_trace_entry* trace;
+    int trace_cap;
 };
 // Dynamic shared memory the launch needs, and the grid (all resident CTAs).
 size_t persist_smem(int max_D, int seg_warp);

@@ -23,11 +23,12 @@ __device__ __forceinline__ unsigned digit_of(unsigned bits, int d) {
     return d == 0 ? (bits >> 21) : d == 1 ? ((bits >> 10) & 2047u) : (bits & 1023u);
 }
 
-// Bin of `hist` (256*PER bins) holding rank `rank`, and the rank inside it.
-// 256 threads; parallel prefix sum over the per-thread bin groups.
-template <int PER>
+// Bin of `hist` (BINS bins) holding rank `rank`, and the rank inside it.
+// NT threads (128 or 256); parallel prefix sum over the per-thread bin groups.
+template <int BINS, int NT>
 __device__ void find_bin(const unsigned* hist, unsigned rank, unsigned& bin, unsigned& rem) {
-    __shared__ unsigned wsum[8];
+    constexpr int PER = BINS / NT, NW = NT / 32;
+    __shared__ unsigned wsum[NW];
     __shared__ unsigned res[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned loc[PER], s = 0;
@@ -42,17 +43,17 @@ __device__ void find_bin(const unsigned* hist, unsigned rank, unsigned& bin, uns
         const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (tid == 0) { res[0] = 256 * PER - 1; res[1] = 0; }
+    if (tid == 0) { res[0] = BINS - 1; res[1] = 0; }
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        unsigned w = lane < 8 ? wsum[lane] : 0u, v = w;
+        unsigned w = lane < NW ? wsum[lane] : 0u, v = w;
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
+        for (int o = 1; o < NW; o <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += y;
         }
-        if (lane < 8) wsum[lane] = v - w;      // exclusive prefix of the warps
+        if (lane < NW) wsum[lane] = v - w;     // exclusive prefix of the warps
     }
     __syncthreads();
     const unsigned incl = x + wsum[warp], excl = incl - s;
@@ -88,6 +89,8 @@ __device__ bool last_block(unsigned* counter, unsigned total) {
 
 // d2 for one upper-triangle tile pair (bi <= bj), mirrored into the lower
 // triangle; histogram of digit 0 over i < j.  The last CTA picks digit 0.
+// NT threads (128 or 256): each owns 32*32/NT entries of one tile row.
+template <int NT = 256>
 __device__ __forceinline__ void pairwise_body(const float* __restrict__ theta, int N, int D,
                                               float* __restrict__ d2, unsigned* __restrict__ hist,
                                               unsigned* __restrict__ sel,
@@ -107,20 +110,23 @@ __device__ __forceinline__ void pairwise_body(const float* __restrict__ theta, i
         B[r * ld + d] = (j0 + r < N) ? theta[(size_t)(j0 + r) * D + d] : 0.f;
     }
     __syncthreads();
-    const int r = threadIdx.x / 8, c0 = threadIdx.x % 8;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    constexpr int TPR = NT / kTile, CPT = kTile / TPR;   // threads per row, columns per thread
+    const int r = threadIdx.x / TPR, c0 = threadIdx.x % TPR;
+    float acc[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q] = 0.f;
     for (int d = 0; d < D; ++d) {
         const float a = A[r * ld + d];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float e = a - B[(c0 + 8 * q) * ld + d];
+        for (int q = 0; q < CPT; ++q) {
+            const float e = a - B[(c0 + TPR * q) * ld + d];
             acc[q] = fmaf(e, e, acc[q]);
         }
     }
     const int i = i0 + r;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int c = c0 + 8 * q, j = j0 + c;
+    for (int q = 0; q < CPT; ++q) {
+        const int c = c0 + TPR * q, j = j0 + c;
         tile[r][c] = acc[q];
         if (i < N && j < N) {
             d2[(size_t)i * N + j] = acc[q];
@@ -141,13 +147,15 @@ __device__ __forceinline__ void pairwise_body(const float* __restrict__ theta, i
             return;
         }
         unsigned b0, r0;
-        find_bin<kBins0 / 256>(hist, median_rank(N), b0, r0);
+        find_bin<kBins0, NT>(hist, median_rank(N), b0, r0);
         if (threadIdx.x == 0) { sel[0] = b0; sel[1] = r0; }
     }
 }
 
 // Histogram of digit `dg` (1 or 2) over the i<j entries whose higher digits
 // match the prefix chosen so far; rows of the upper triangle, grid-strided.
+// NT threads (128 or 256).
+template <int NT = 256>
 __device__ __forceinline__ void median_digit_body(int N, int dg, const float* __restrict__ d2,
                                                   unsigned* __restrict__ hist,
                                                   unsigned* __restrict__ sel,
@@ -175,11 +183,11 @@ __device__ __forceinline__ void median_digit_body(int N, int dg, const float* __
     if (last_block(counter, (unsigned)ctas)) {
         if (dg == 1) {
             unsigned b1n, r1;
-            find_bin<kBins1 / 256>(out, __ldcg(sel + 1), b1n, r1);
+            find_bin<kBins1, NT>(out, __ldcg(sel + 1), b1n, r1);
             if (threadIdx.x == 0) { sel[2] = b1n; sel[3] = r1; }
         } else {
             unsigned b2, r2;
-            find_bin<kBins2 / 256>(out, __ldcg(sel + 3), b2, r2);
+            find_bin<kBins2, NT>(out, __ldcg(sel + 3), b2, r2);
             if (threadIdx.x == 0) {
                 const float med = __uint_as_float((b0 << 21) | (b1 << 10) | b2);
                 float h = med / logf((float)N + 1.f);

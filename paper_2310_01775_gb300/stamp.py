@@ -111,6 +111,8 @@ _sigs = {
     "stamp_batch_get_persistent": [_vp, _vp, _vp, _vp],
     "stamp_batch_inject_wait_timeout": [_vp],
     "stamp_batch_read_grad": [_vp, _i, _vp],
+    "stamp_batch_set_trace": [_vp, _i],
+    "stamp_batch_read_trace": [_vp, _vp, _i, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     getattr(_lib, _name).argtypes = _args
@@ -362,6 +364,26 @@ class Problem:
                                          _f32(adam_v, "adam_v"), step, lr, int(sgd_phase),
                                          _f32(h_out, "h_out"), _f32(phi_out, "phi_out")))
 
+    def set_trace(self, on: bool):
+        """Record every persistent launch's work items (stamp_batch_set_trace)."""
+        _check(_lib.stamp_batch_set_trace(self.handle, int(bool(on))))
+
+    def read_trace(self) -> dict:
+        """The last persistent launch's items: kind, SM and claim / start /
+        end times in ns (from the first claim)."""
+        n, kinds = ctypes.c_int(), (ctypes.c_int * 5)()
+        _check(_lib.stamp_batch_read_trace(self.handle, None, 0, ctypes.byref(n), kinds))
+        raw = np.zeros((n.value, 4), dtype=np.uint64)   # 3 x u64 times, then (item, sm)
+        _check(_lib.stamp_batch_read_trace(self.handle, raw.ctypes.data, n.value, None, None))
+        t = raw[:, :3].astype(np.int64)
+        item_sm = np.ascontiguousarray(raw[:, 3]).view(np.uint32).reshape(-1, 2)
+        bounds = np.cumsum([0, kinds[0], kinds[1], kinds[2], kinds[2], kinds[3], kinds[4]])
+        names = np.array(["rollout", "pairwise", "median1", "median2", "stein", "adam"])
+        kind = names[np.searchsorted(bounds, np.arange(n.value), side="right") - 1]
+        t0 = t[t[:, 0] > 0, 0].min() if (t[:, 0] > 0).any() else 0
+        return {"kind": kind, "item": item_sm[:, 0], "sm": item_sm[:, 1],
+                "claim": t[:, 0] - t0, "start": t[:, 1] - t0, "end": t[:, 2] - t0}
+
     def inject_wait_timeout(self):
         """Test hook: the next Stein-direction launch's first copy is never
         issued and its bounded wait runs out (STAMP_ETIMEOUT at the next sync)."""
@@ -583,6 +605,26 @@ class Batch:
         _check(_lib.stamp_batch_get_persistent(self.handle, ctypes.byref(on), ctypes.byref(a),
                                                ctypes.byref(p)))
         return bool(on.value), a.value, p.value
+
+    def set_trace(self, on: bool):
+        """Record every persistent launch's work items (stamp_batch_set_trace)."""
+        _check(_lib.stamp_batch_set_trace(self.handle, int(bool(on))))
+
+    def read_trace(self) -> dict:
+        """The last persistent launch's items: kind, SM and claim / start /
+        end times in ns (from the first claim)."""
+        n, kinds = ctypes.c_int(), (ctypes.c_int * 5)()
+        _check(_lib.stamp_batch_read_trace(self.handle, None, 0, ctypes.byref(n), kinds))
+        raw = np.zeros((n.value, 4), dtype=np.uint64)   # 3 x u64 times, then (item, sm)
+        _check(_lib.stamp_batch_read_trace(self.handle, raw.ctypes.data, n.value, None, None))
+        t = raw[:, :3].astype(np.int64)
+        item_sm = np.ascontiguousarray(raw[:, 3]).view(np.uint32).reshape(-1, 2)
+        bounds = np.cumsum([0, kinds[0], kinds[1], kinds[2], kinds[2], kinds[3], kinds[4]])
+        names = np.array(["rollout", "pairwise", "median1", "median2", "stein", "adam"])
+        kind = names[np.searchsorted(bounds, np.arange(n.value), side="right") - 1]
+        t0 = t[t[:, 0] > 0, 0].min() if (t[:, 0] > 0).any() else 0
+        return {"kind": kind, "item": item_sm[:, 0], "sm": item_sm[:, 1],
+                "claim": t[:, 0] - t0, "start": t[:, 1] - t0, "end": t[:, 2] - t0}
 
     def inject_wait_timeout(self):
         """The next persistent solve's dependency waits run out (error-path test)."""
