@@ -239,3 +239,27 @@ def test_full_size_persistent_gradients_sampled():
     _grad_bar(insts, _grads(b, insts), phys, 100, {nb: 1 for nb in range(1, 5)},
               sample={g: (8 if nb == 4 else 12) for nb, g in pick.items()})
     b.close()
+
+
+def test_trace_records_every_item_in_dependency_order():
+    """stamp_batch_set_trace: every work item of the last launch is recorded
+    once, with claim <= dependencies met <= end; a median pass, Stein block
+    or Adam chunk starts only after its instance's earlier items, so each
+    kind's first start follows the first end of the kind it waits on."""
+    insts = _instances(50)
+    b = _batch(insts, 50)
+    b.set_trace(True)
+    b.solve(2, 1e-2, use_graph=True)
+    tr = b.read_trace()
+    n = len(tr["kind"])
+    assert n > 0 and np.array_equal(np.sort(tr["item"]), np.arange(n))
+    assert (tr["claim"] >= 0).all() and (tr["start"] >= tr["claim"]).all()
+    assert (tr["end"] >= tr["start"]).all()
+    first_end = {k: tr["end"][tr["kind"] == k].min() for k in set(tr["kind"])}
+    first_start = {k: tr["start"][tr["kind"] == k].min() for k in set(tr["kind"])}
+    for later, earlier in (("median1", "pairwise"), ("median2", "median1"), ("stein", "median2"),
+                           ("stein", "rollout"), ("adam", "stein")):
+        assert first_start[later] >= first_end[earlier], (later, earlier)
+    assert set(np.unique(tr["sm"])) <= set(range(1024))
+    b.set_trace(False)
+    b.close()
