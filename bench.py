@@ -41,7 +41,7 @@ FP32_LANES = 128                    # FP32 lanes per SM; 1 FMA = 2 FLOP
 # sweep: its replay and sweep launches together), from one cold-cache ncu
 # capture of the workload, valid while the kernel sources are unchanged
 # (sha256 prefix over the rollout sources at capture time).
-TRAFFIC = {("pusher3_h6", "rollout_adj"): ("ee95a14a7ddb538b", 181.50e6)}   # replay + sweep
+TRAFFIC = {("pusher3_h6", "rollout_adj"): ("243c7f35e3b01a4a", 179.97e6)}   # replay + sweep
 ROLLOUT_SOURCES = ("rollout.cuh", "adjoint_time.cu")
 
 
