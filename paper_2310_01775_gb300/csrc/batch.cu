@@ -143,7 +143,7 @@ struct stamp_batch {
     stamp::PersistArgs pa{};
     SimConst cls_sc[stamp::kMaxBlocks]{};
     BatchInst* p_inst = nullptr;
-    int4 *p_need = nullptr, *p_warps = nullptr, *p_phi = nullptr;
+    int4 *p_need = nullptr, *p_warps = nullptr, *p_phi = nullptr, *p_pw = nullptr;
     int2* p_adam = nullptr;
     unsigned *p_ctr = nullptr, *p_dep = nullptr;
     int extra_wait = 0;              // > 0 for the next solve: its Stein items' waits run out
@@ -329,14 +329,21 @@ stamp_status build_persist_queue(stamp_batch* b, const std::vector<SvgdInst>& si
     constexpr int W = stamp::kPersistWarps;
     struct Task { double t; int g, first, nb; };
     std::vector<Task> tasks;
-    std::vector<int4> need(b->n);
+    std::vector<int4> need(b->n), pw;
     for (int g = 0; g < b->n; ++g) {
         const stamp_instance_desc& d = b->inst[g];
         const int tpw = 32 / stamp::persist_lanes(d.n_blocks);
         const int warps = (d.N + tpw - 1) / tpw;
         for (int w = 0; w < warps; ++w) tasks.push_back({d.H * kCost[d.n_blocks - 1], g, w * tpw, d.n_blocks});
         const int rb = (d.N + stamp::kPersistRows - 1) / stamp::kPersistRows;
-        need[g] = make_int4(warps, si[g].nt * (si[g].nt + 1) / 2, si[g].med_ctas, si[g].shares * rb);
+        // pairwise strips: up to kPersistStrip tile pairs of one tile row each
+        int strips = 0;
+        for (int bi = 0; bi < si[g].nt; ++bi)
+            for (int bj = bi; bj < si[g].nt; bj += stamp::kPersistStrip) {
+                pw.push_back(make_int4(g, bi, bj, std::min(bj + stamp::kPersistStrip, si[g].nt)));
+                ++strips;
+            }
+        need[g] = make_int4(warps, strips, si[g].med_ctas, si[g].shares * rb);
     }
     // by block count (consecutive items on an SM run the same code), longest first within it
     std::stable_sort(tasks.begin(), tasks.end(), [](const Task& x, const Task& y) {
@@ -376,6 +383,8 @@ stamp_status build_persist_queue(stamp_batch* b, const std::vector<SvgdInst>& si
     B_CUDA(cudaMalloc(&b->p_warps, warps.size() * sizeof(int4)));
     B_CUDA(cudaMalloc(&b->p_phi, phi.size() * sizeof(int4)));
     B_CUDA(cudaMalloc(&b->p_adam, adam.size() * sizeof(int2)));
+    B_CUDA(cudaMalloc(&b->p_pw, pw.size() * sizeof(int4)));
+    B_CUDA(cudaMemcpy(b->p_pw, pw.data(), pw.size() * sizeof(int4), cudaMemcpyHostToDevice));
     B_CUDA(cudaMemcpy(b->p_warps, warps.data(), warps.size() * sizeof(int4), cudaMemcpyHostToDevice));
     B_CUDA(cudaMemcpy(b->p_phi, phi.data(), phi.size() * sizeof(int4), cudaMemcpyHostToDevice));
     B_CUDA(cudaMemcpy(b->p_adam, adam.data(), adam.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -385,12 +394,12 @@ stamp_status build_persist_queue(stamp_batch* b, const std::vector<SvgdInst>& si
     pa.sinst = b->sinst;
     pa.need = b->p_need;
     pa.warps = b->p_warps;
-    pa.pw = b->pw_items;
+    pa.pw = b->p_pw;
     pa.med = b->med_items;
     pa.phi = b->p_phi;
     pa.adam = b->p_adam;
     pa.n_roll = n_roll;
-    pa.n_pw = b->n_pw;
+    pa.n_pw = (int)pw.size();
     pa.n_med = b->n_med;
     pa.n_phi = (int)phi.size();
     pa.n_adam = (int)adam.size();
@@ -645,6 +654,7 @@ void stamp_batch_destroy(stamp_batch* b) {
     cudaFree(b->p_warps);
     cudaFree(b->p_phi);
     cudaFree(b->p_adam);
+    cudaFree(b->p_pw);
     cudaFree(b->trace);
     cudaFree(b->arena);
     if (b->ev_join) cudaEventDestroy(b->ev_join);

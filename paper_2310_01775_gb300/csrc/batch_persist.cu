@@ -14,7 +14,8 @@
 //                     launches, lanes fixed per block count; the CTA's warps
 //                     all finish their forwards before the adjoints start
 //                     (one loop body in the SM's instruction cache at a time);
-//   pairwise tiles    d2 and the median's first radix digit;
+//   pairwise strips   d2 for up to four tile pairs of one tile row, and the
+//                     median's first radix digit;
 //   median CTAs       the second digit, then the third (h);
 //   Stein blocks      phi for 32 rows and one j-share (Eq. svgd);
 //   Adam chunks       4096 elements of theta, m, v (the shares summed in
@@ -139,18 +140,39 @@ __device__ __forceinline__ void adam_chunk(const PersistArgs& p, const SvgdInst&
     const long long e0 = b0 + kPersistAdamChunk < ne ? b0 + kPersistAdamChunk : ne;
     const float2 b12 = p.bc[*p.step + 1];
     const float bc1 = b12.x, bc2 = b12.y;
-    for (long long loc = b0 + threadIdx.x; loc < e0; loc += kPersistThreads) {
-        const long long t = s.elem0 + loc;
-        float phi = s.part[loc];
-        for (int q = 1; q < s.shares; ++q) phi += s.part[(size_t)q * ne + loc];
-        const float gr = -phi;
-        const float mt = 0.9f * p.m[t] + 0.1f * gr;
-        const float vt = 0.999f * p.v[t] + 0.001f * gr * gr;
-        const float th = p.theta[t] - p.lr * (mt / bc1) / (sqrtf(vt / bc2) + 1e-8f);
-        p.m[t] = mt;
-        p.v[t] = vt;
-        p.theta[t] = th;
-        if (!isfinite(th) || !isfinite(gr)) atomicOr(p.flag, 1);
+    // four elements per thread at a time: every load before any store, so
+    // the loads are in flight together (the stores may alias them)
+    constexpr int U = 4;
+    for (long long l0 = b0 + threadIdx.x; l0 < e0; l0 += U * kPersistThreads) {
+        float phi[U], m0[U], v0[U], t0[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long loc = l0 + u * kPersistThreads, t = s.elem0 + loc;
+            const bool ok = loc < e0;
+            phi[u] = ok ? s.part[loc] : 0.f;
+            m0[u] = ok ? p.m[t] : 0.f;
+            v0[u] = ok ? p.v[t] : 0.f;
+            t0[u] = ok ? p.theta[t] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long loc = l0 + u * kPersistThreads;
+            if (loc < e0)
+                for (int q = 1; q < s.shares; ++q) phi[u] += s.part[(size_t)q * ne + loc];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long loc = l0 + u * kPersistThreads, t = s.elem0 + loc;
+            if (loc >= e0) continue;
+            const float gr = -phi[u];
+            const float mt = 0.9f * m0[u] + 0.1f * gr;
+            const float vt = 0.999f * v0[u] + 0.001f * gr * gr;
+            const float th = t0[u] - p.lr * (mt / bc1) / (sqrtf(vt / bc2) + 1e-8f);
+            p.m[t] = mt;
+            p.v[t] = vt;
+            p.theta[t] = th;
+            if (!isfinite(th) || !isfinite(gr)) atomicOr(p.flag, 1);
+        }
     }
 }
 
@@ -219,8 +241,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             const int4 it = p.pw[k - e_roll];
             if (p.active[it.x]) {
                 const SvgdInst& s = p.sinst[it.x];
-                pairwise_body<kPersistThreads>(s.theta, s.N, s.D, s.d2, s.hist, s.sel, s.counter,
-                                               s.h, it.y, it.z, s.nt);
+                pairwise_strip_body<kPersistThreads>(s.theta, s.N, s.D, s.d2, s.hist, s.sel,
+                                                     s.counter, s.h, it.y, it.z, it.w,
+                                                     (unsigned)p.need[it.x].y);
                 cta_signal(p.dep + (size_t)kPersistDeps * it.x + 1);
             }
         } else if (k < e_m2) {

@@ -234,6 +234,7 @@ constexpr int kPersistWarps = kPersistThreads / 32;
 constexpr int kPersistRows = kPersistWarps * 4;   // Stein-direction rows per item
 constexpr int kPersistAdamChunk = 4096;           // particle elements per Adam item
 constexpr int kPersistDeps = 5;                   // completion counters per instance
+constexpr int kPersistStrip = 4;                  // pairwise tile pairs per item (one tile row)
 // lanes per particle team in the persistent kernel, by block count
 __host__ __device__ constexpr int persist_lanes(int nb) { return nb == 1 ? 2 : nb == 2 ? 4 : 8; }
 // Stein-direction column slots per lane for the batch's largest D
@@ -243,7 +244,7 @@ struct PersistArgs {
     const SvgdInst* sinst;  // per batch instance
     const int4* need;       // per instance: rollout warps, pairwise tiles, median CTAs, Stein items
     const int4* warps;      // kPersistWarps per rollout item: (instance or -1, first particle, n_blocks, 0)
-    const int4* pw;         // (instance, tile row, tile column, 0)
+    const int4* pw;         // (instance, tile row, first and end tile column of a strip)
     const int2* med;        // (instance, CTA), for both median digits
     const int4* phi;        // (instance, row block of kPersistRows, j-share, 0)
     const int2* adam;       // (instance, chunk)

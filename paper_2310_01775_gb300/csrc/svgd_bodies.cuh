@@ -87,61 +87,73 @@ __device__ bool last_block(unsigned* counter, unsigned total) {
     return last;
 }
 
-// d2 for one upper-triangle tile pair (bi <= bj), mirrored into the lower
-// triangle; histogram of digit 0 over i < j.  The last CTA picks digit 0.
-// NT threads (128 or 256): each owns 32*32/NT entries of one tile row.
+// d2 for the upper-triangle tile pairs (bi, bj), bj0 <= bj < bj1 (bi <= bj0),
+// mirrored into the lower triangle; histogram of digit 0 over i < j.  The
+// last of the instance's `items` CTAs to finish picks digit 0.  NT threads
+// (128 or 256): each owns 32*32/NT entries of one tile row.  A strip of
+// several tiles reuses the row tile A and flushes the histogram once.
 template <int NT = 256>
-__device__ __forceinline__ void pairwise_body(const float* __restrict__ theta, int N, int D,
-                                              float* __restrict__ d2, unsigned* __restrict__ hist,
-                                              unsigned* __restrict__ sel,
-                                              unsigned* __restrict__ counter,
-                                              float* __restrict__ h_dev, int bi, int bj, int nt) {
+__device__ __forceinline__ void pairwise_strip_body(const float* __restrict__ theta, int N, int D,
+                                                    float* __restrict__ d2,
+                                                    unsigned* __restrict__ hist,
+                                                    unsigned* __restrict__ sel,
+                                                    unsigned* __restrict__ counter,
+                                                    float* __restrict__ h_dev, int bi, int bj0,
+                                                    int bj1, unsigned items) {
     extern __shared__ float sm[];
     const int ld = D + 1;                        // padded rows: conflict-free column walks
     float* A = sm;
     float* B = sm + kTile * ld;
     __shared__ unsigned h0[kBins0];
     __shared__ float tile[kTile][kTile + 1];
-    const int i0 = bi * kTile, j0 = bj * kTile;
+    const int i0 = bi * kTile;
     for (int t = threadIdx.x; t < kBins0; t += blockDim.x) h0[t] = 0u;
     for (int t = threadIdx.x; t < kTile * D; t += blockDim.x) {
         const int r = t / D, d = t % D;
         A[r * ld + d] = (i0 + r < N) ? theta[(size_t)(i0 + r) * D + d] : 0.f;
-        B[r * ld + d] = (j0 + r < N) ? theta[(size_t)(j0 + r) * D + d] : 0.f;
     }
-    __syncthreads();
     constexpr int TPR = NT / kTile, CPT = kTile / TPR;   // threads per row, columns per thread
     const int r = threadIdx.x / TPR, c0 = threadIdx.x % TPR;
-    float acc[CPT];
+    for (int bj = bj0; bj < bj1; ++bj) {
+        const int j0 = bj * kTile;
+        // the previous tile's compute is done (barrier before its mirror)
+        for (int t = threadIdx.x; t < kTile * D; t += blockDim.x) {
+            const int rr = t / D, d = t % D;
+            B[rr * ld + d] = (j0 + rr < N) ? theta[(size_t)(j0 + rr) * D + d] : 0.f;
+        }
+        __syncthreads();
+        float acc[CPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) acc[q] = 0.f;
-    for (int d = 0; d < D; ++d) {
-        const float a = A[r * ld + d];
+        for (int q = 0; q < CPT; ++q) acc[q] = 0.f;
+        for (int d = 0; d < D; ++d) {
+            const float a = A[r * ld + d];
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const float e = a - B[(c0 + TPR * q) * ld + d];
+                acc[q] = fmaf(e, e, acc[q]);
+            }
+        }
+        const int i = i0 + r;
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
-            const float e = a - B[(c0 + TPR * q) * ld + d];
-            acc[q] = fmaf(e, e, acc[q]);
+            const int c = c0 + TPR * q, j = j0 + c;
+            tile[r][c] = acc[q];
+            if (i < N && j < N) {
+                d2[(size_t)i * N + j] = acc[q];
+                if (i < j) atomicAdd(&h0[digit_of(__float_as_uint(acc[q]), 0)], 1u);
+            }
         }
+        __syncthreads();
+        if (bi != bj)   // mirror: coalesced rows of the lower triangle
+            for (int t = threadIdx.x; t < kTile * kTile; t += blockDim.x) {
+                const int rr = t / kTile, cc = t % kTile;   // rr indexes j, cc indexes i
+                if (j0 + rr < N && i0 + cc < N) d2[(size_t)(j0 + rr) * N + i0 + cc] = tile[cc][rr];
+            }
+        __syncthreads();   // tile and B are free for the next pair
     }
-    const int i = i0 + r;
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-        const int c = c0 + TPR * q, j = j0 + c;
-        tile[r][c] = acc[q];
-        if (i < N && j < N) {
-            d2[(size_t)i * N + j] = acc[q];
-            if (i < j) atomicAdd(&h0[digit_of(__float_as_uint(acc[q]), 0)], 1u);
-        }
-    }
-    __syncthreads();
-    if (bi != bj)   // mirror: coalesced rows of the lower triangle
-        for (int t = threadIdx.x; t < kTile * kTile; t += blockDim.x) {
-            const int rr = t / kTile, cc = t % kTile;   // rr indexes j, cc indexes i
-            if (j0 + rr < N && i0 + cc < N) d2[(size_t)(j0 + rr) * N + i0 + cc] = tile[cc][rr];
-        }
     for (int t = threadIdx.x; t < kBins0; t += blockDim.x)
         if (h0[t]) atomicAdd(&hist[t], h0[t]);
-    if (last_block(counter, (unsigned)(nt * (nt + 1) / 2))) {
+    if (last_block(counter, items)) {
         if (N < 2) {
             if (threadIdx.x == 0) *h_dev = 1.f;
             return;
@@ -150,6 +162,17 @@ __device__ __forceinline__ void pairwise_body(const float* __restrict__ theta, i
         find_bin<kBins0, NT>(hist, median_rank(N), b0, r0);
         if (threadIdx.x == 0) { sel[0] = b0; sel[1] = r0; }
     }
+}
+
+// One tile pair per CTA: the nt(nt+1)/2 CTAs of an instance.
+template <int NT = 256>
+__device__ __forceinline__ void pairwise_body(const float* __restrict__ theta, int N, int D,
+                                              float* __restrict__ d2, unsigned* __restrict__ hist,
+                                              unsigned* __restrict__ sel,
+                                              unsigned* __restrict__ counter,
+                                              float* __restrict__ h_dev, int bi, int bj, int nt) {
+    pairwise_strip_body<NT>(theta, N, D, d2, hist, sel, counter, h_dev, bi, bj, bj + 1,
+                            (unsigned)(nt * (nt + 1) / 2));
 }
 
 // Histogram of digit `dg` (1 or 2) over the i<j entries whose higher digits
@@ -169,11 +192,27 @@ __device__ __forceinline__ void median_digit_body(int N, int dg, const float* __
     const int nb = dg == 1 ? kBins1 : kBins2;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) hloc[t] = 0u;
     __syncthreads();
-    for (int i = cta; i < N - 1; i += ctas) {
+    // two of the CTA's rows at a time, four entries of each per thread: the
+    // eight loads are in flight together (the row i2 > i is the shorter)
+    constexpr int U = 4;
+    for (int i = cta; i < N - 1; i += 2 * ctas) {
+        const int i2 = i + ctas;
         const float* row = d2 + (size_t)i * N;
-        for (int j = i + 1 + threadIdx.x; j < N; j += blockDim.x) {
-            const unsigned bits = __float_as_uint(row[j]);
-            if ((bits >> shift) == prefix) atomicAdd(&hloc[digit_of(bits, dg)], 1u);
+        const float* row2 = d2 + (size_t)(i2 < N - 1 ? i2 : i) * N;
+        for (int j0 = threadIdx.x; i + 1 + j0 < N; j0 += U * NT) {
+            unsigned bits[2 * U];
+            bool ok[2 * U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = i + 1 + j0 + u * NT, k = i2 + 1 + j0 + u * NT;
+                ok[u] = j < N;
+                ok[U + u] = i2 < N - 1 && k < N;
+                bits[u] = ok[u] ? __float_as_uint(row[j]) : 0u;
+                bits[U + u] = ok[U + u] ? __float_as_uint(row2[k]) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 2 * U; ++u)
+                if (ok[u] && (bits[u] >> shift) == prefix) atomicAdd(&hloc[digit_of(bits[u], dg)], 1u);
         }
     }
     __syncthreads();
