@@ -14,7 +14,7 @@
 //                     launches, lanes fixed per block count; the CTA's warps
 //                     all finish their forwards before the adjoints start
 //                     (one loop body in the SM's instruction cache at a time);
-//   pairwise strips   d2 for up to four tile pairs of one tile row, and the
+//   pairwise strips   d2 for up to eight tile pairs of one tile row, and the
 //                     median's first radix digit;
 //   median CTAs       the second digit, then the third (h);
 //   Stein blocks      phi for 32 rows and one j-share (Eq. svgd);

@@ -234,7 +234,7 @@ constexpr int kPersistWarps = kPersistThreads / 32;
 constexpr int kPersistRows = kPersistWarps * 4;   // Stein-direction rows per item
 constexpr int kPersistAdamChunk = 4096;           // particle elements per Adam item
 constexpr int kPersistDeps = 5;                   // completion counters per instance
-constexpr int kPersistStrip = 4;                  // pairwise tile pairs per item (one tile row)
+constexpr int kPersistStrip = 8;                  // pairwise tile pairs per item (one tile row)
 // lanes per particle team in the persistent kernel, by block count
 __host__ __device__ constexpr int persist_lanes(int nb) { return nb == 1 ? 2 : nb == 2 ? 4 : 8; }
 // Stein-direction column slots per lane for the batch's largest D
