@@ -199,7 +199,7 @@ def surrogate_vs_plain(stream, seeds=(3, 4, 5)):
 
 
 def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3, check_every=10,
-                    screen=True):
+                    screen=True, seed=0):
     """256 seeded uneven instances (1-4 blocks, H 2-8, N log-uniform 64-1024,
     T=100; goals planted: the end poses of a hard rollout of a random plan)
     solved together: autotuned launch configuration and launch mode (per-class
@@ -210,12 +210,12 @@ def batched_serving(stream, peak_tflops, peak_src, n=256, iters=500, target=1e-3
     import torch
     from paper_2310_01775_gb300 import stamp as S
     from paper_2310_01775_gb300 import workloads as W
-    insts = W.batch_instances(n)
+    insts = W.batch_instances(n, seed)
     for g, d in enumerate(insts):   # plant each goal
         P = dict(W.PHYSICS, n_blocks=d["n_blocks"], H=d["H"], T=100, ckpt_every=100)
         D = d["H"] * (4 * d["n_blocks"] + 2)
         prob = S.Problem(P, d["init"], d["init"], 1, stream)
-        plan = torch.tensor(3.0 * W.random_theta(1, D, 9000 + g), device="cuda")
+        plan = torch.tensor(3.0 * W.random_theta(1, D, 9000 + 1000 * seed + g), device="cuda")
         c = torch.empty(1, device="cuda")
         fin = torch.empty(1, 6 * d["n_blocks"], device="cuda")
         prob.rollout_fwd(plan, 1, 0, -1, 1, c, fin)
