@@ -263,3 +263,20 @@ def test_trace_records_every_item_in_dependency_order():
     assert set(np.unique(tr["sm"])) <= set(range(1024))
     b.set_trace(False)
     b.close()
+
+
+def test_persistent_largest_parameter_count_matches_per_class():
+    """A 4-block, 16-action instance (D = 288: the Stein blocks' widest
+    column layout and the largest shared-memory plan) beside a small one,
+    softer contact, two iterations in each mode: particles to 1e-4."""
+    T, iters, lr = 50, 2, 1e-2
+    phys = dict(W.PHYSICS, **SOFT)
+    insts = _instances(T, phys, [(4, 16, 40), (1, 2, 33)], 80, 3000)
+    a, p = _batch(insts, T, False, phys), _batch(insts, T, True, phys)
+    a.solve(iters, lr)
+    p.solve(iters, lr)
+    for g, (x, y) in enumerate(zip(_theta(a, insts), _theta(p, insts))):
+        assert x.shape[1] == (288 if g == 0 else 12)
+        assert float((x - y).abs().max()) <= 1e-4, (g, float((x - y).abs().max()))
+    a.close()
+    p.close()
