@@ -255,7 +255,7 @@ using async::tma_load_1d;
 // memory stages with 1-D TMA bulk copies (mbarrier completion), one tile
 // ahead of the compute.  The d2 values of the next tile are prefetched into
 // registers; k_ij for the warp's rows is one float4 per j (a broadcast load).
-constexpr int kR = 4, kW = 2, kTJ = 32;
+constexpr int kR = 4, kW = 8, kTJ = 32;   // rows per warp, warps per CTA, j rows per tile
 __host__ __device__ constexpr int phi_stage_floats(int D, int DP) {
     return ((kTJ * D + 32 * DP) + 3) / 4 * 4;   // per array, 16-byte multiple
 }
@@ -361,7 +361,8 @@ __device__ __forceinline__ bool phi_body(const float* __restrict__ theta,
         phases ^= 1u << s;
         const float* Tj = sm + 2 * s * sf;
         const float* Gj = Tj + sf;
-        for (int jj = 0; jj < nj; ++jj) {
+#pragma unroll 4
+        for (int jj = 0; jj < nj; ++jj) {   // several j's shared-memory loads in flight
             const float4 k4 = Ks[warp * kTJ + jj];
             const float kk[kR] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
