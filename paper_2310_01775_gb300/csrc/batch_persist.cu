@@ -180,15 +180,15 @@ __device__ __forceinline__ bool run_phi(const PersistArgs& p, const SvgdInst& s,
                                         int share) {
     switch (p.dp) {
         case 3:
-            return phi_body<3, kPersistWarps>(s.theta, s.grad, s.N, s.D, s.d2, s.h, s.part,
+            return phi_body<3, kPersistWarps, 1>(s.theta, s.grad, s.N, s.D, s.d2, s.h, s.part,
                                               s.j_chunk, p.flag, rblock, share, nullptr,
                                               kWaitLimit, false, 0, s.N);
         case 6:
-            return phi_body<6, kPersistWarps>(s.theta, s.grad, s.N, s.D, s.d2, s.h, s.part,
+            return phi_body<6, kPersistWarps, 1>(s.theta, s.grad, s.N, s.D, s.d2, s.h, s.part,
                                               s.j_chunk, p.flag, rblock, share, nullptr,
                                               kWaitLimit, false, 0, s.N);
         default:
-            return phi_body<9, kPersistWarps>(s.theta, s.grad, s.N, s.D, s.d2, s.h, s.part,
+            return phi_body<9, kPersistWarps, 1>(s.theta, s.grad, s.N, s.D, s.d2, s.h, s.part,
                                               s.j_chunk, p.flag, rblock, share, nullptr,
                                               kWaitLimit, false, 0, s.N);
     }

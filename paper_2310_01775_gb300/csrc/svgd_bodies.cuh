@@ -259,10 +259,11 @@ constexpr int kR = 4, kW = 8, kTJ = 32;   // rows per warp, warps per CTA, j row
 __host__ __device__ constexpr int phi_stage_floats(int D, int DP) {
     return ((kTJ * D + 32 * DP) + 3) / 4 * 4;   // per array, 16-byte multiple
 }
-// KW warps per CTA (kW in the per-piece kernels); false if a copy never
+// KW warps per CTA (kW in the per-piece kernels), the j loop unrolled
+// UNROLL times; false if a copy never
 // landed (error bit 2 set).  A CTA that goes on to other work may reuse the
 // shared memory: the mbarriers are invalidated on the way out.
-template <int DP, int KW = kW>
+template <int DP, int KW = kW, int UNROLL = 4>
 __device__ __forceinline__ bool phi_body(const float* __restrict__ theta,
                                          const float* __restrict__ grad, int N, int D,
                                          const float* __restrict__ d2,
@@ -361,7 +362,7 @@ __device__ __forceinline__ bool phi_body(const float* __restrict__ theta,
         phases ^= 1u << s;
         const float* Tj = sm + 2 * s * sf;
         const float* Gj = Tj + sf;
-#pragma unroll 4
+#pragma unroll (UNROLL)
         for (int jj = 0; jj < nj; ++jj) {   // several j's shared-memory loads in flight
             const float4 k4 = Ks[warp * kTJ + jj];
             const float kk[kR] = {k4.x, k4.y, k4.z, k4.w};
