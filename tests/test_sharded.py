@@ -1,4 +1,4 @@
-"""Particle shards of one Stein iteration on CPU ranks (two gloo processes).
+"""Particle shards of one Stein iteration on CPU ranks (two and three gloo processes).
 
 The sharded driver (paper_2310_01775_gb300/sharded.py) splits N particles
 into contiguous shards, all-gathers theta and grad log rho once per
@@ -13,6 +13,7 @@ import socket
 import sys
 
 import numpy as np
+import pytest
 import torch
 import torch.multiprocessing as mp
 
@@ -92,20 +93,22 @@ def test_partition_is_contiguous_and_balanced():
             assert max(r for _, r in parts) - min(r for _, r in parts) <= 1
 
 
-def test_two_gloo_shards_equal_the_unsharded_solve_bit_for_bit():
+@pytest.mark.parametrize("world, N", [(2, 33), (3, 34)])   # ragged: 17 + 16, 12 + 11 + 11 rows
+def test_gloo_shards_equal_the_unsharded_solve_bit_for_bit(world, N):
     from oracle import stamp_oracle as O
-    N, seed = 33, 5                                   # ragged: shards of 17 and 16 rows
+    seed = 5
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, N, seed, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, N, seed, q)) for r in range(world)]
     for p in procs:
         p.start()
     got = dict(q.get(timeout=600) for _ in procs)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    assert np.array_equal(got[0], got[1])            # every rank holds the gathered set
+    for r in range(1, world):
+        assert np.array_equal(got[0], got[r])        # every rank holds the gathered set
     P, init, goal = _problem()
     ref = O.solve(P, init, goal, N, SVGD, SGD, seed, LR, k=0)["theta"]
     assert np.array_equal(got[0], ref)
